@@ -1,0 +1,921 @@
+/*
+ * Plain FP64 CPU oracle for the D2Q9 DUGKS / BKG finite-volume step.
+ * TEST INFRASTRUCTURE ONLY: see dvbe_oracle.h for who may use it.
+ *
+ * The step is written in the paper's order with explicit arrays:
+ *   1. cell moments and equilibrium               (Sec 2.1, Eq. macro_var)
+ *   2. phi = f_bar^+ (DUGKS) or f_tilde^+ (BKG)   (Eqs. eq_trans_2, bkg_collision)
+ *   3. ghost layer of phi                         (Sec 2.5)
+ *   4. face values phi(x_b - h xi) by linear reconstruction
+ *                                                 (Eqs. eq_char, bkg_fb, f_left)
+ *   5. wall / inflow treatment at boundary faces  (Sec 2.5)
+ *   6. DUGKS: face moments, back-transform to f   (Sec 2.2 after Eq. eq_char)
+ *   7. flux and update                            (Eqs. eq_update, eq_flux, lwfv, bkg_fv)
+ *
+ * Readings taken where the paper is silent (each also pinned or marked in the
+ * tests):
+ *   - The closed forms of the transforms are derived here from their
+ *     definitions (f_tilde = f - dt/2 Omega, f_bar^+ = f + h/2 Omega, ...):
+ *       f        = (2 tau f_tilde + dt f_eq) / (2 tau + dt)
+ *       f_bar^+  = ((2 tau - h) f_tilde + 3 h f_eq) / (2 tau + dt)
+ *       f_tilde^+= ((2 tau - dt) f_tilde + 2 dt f_eq) / (2 tau + dt)
+ *       f (face) = (2 tau f_bar + h f_eq) / (2 tau + h)
+ *     Pinned by orc_step_implicit, which solves the implicit forms directly.
+ *   - Linear reconstruction on a tensor mesh: at an x-face between cells L, R
+ *     with theta = (x_b - x_L)/(x_R - x_L): value (1-theta) phi_L + theta phi_R,
+ *     normal slope (phi_R - phi_L)/(x_R - x_L), tangential slope the theta
+ *     blend of the two cells' central differences; the foot value is
+ *     value - h (xi . slope).  On a uniform mesh this is exactly Eq. f_left.
+ *   - Flux sign: the update subtracts the outward flux (Eq. bkg_fv).
+ *   - Wall ghosts: linear extrapolation from the first two inner centres to
+ *     the mirror point of the first centre.  Corner ghosts: x sides are filled
+ *     first (interior rows), then y sides over the full padded width.
+ *   - Bounce-back uses the formula of Sec 2.5 literally (no density factor).
+ *   - Diffuse wall (parity unpinned apart from zero normal mass flux): the
+ *     incoming values are f_eq(rho_w, U_w) with rho_w making the normal mass
+ *     flux through the face zero.
+ *   - Inflow: ghosts and all face values are f_eq(rho_inf, U_inf); outflow:
+ *     zero-gradient ghosts; symmetry: mirrored ghosts.
+ */
+#include "dvbe_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Velocity model, Sec 2.1                                            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  double c, cs2;
+  double xi[9][2];
+  double w[9];
+  int opp[9];  /* reverse direction: xi_opp = -xi            */
+  int mirx[9]; /* mirror across an x-normal face: xi_x -> -xi_x */
+  int miry[9]; /* mirror across a y-normal face: xi_y -> -xi_y  */
+} vset;
+
+static void make_vset(double RT, vset *v) {
+  const double pi = acos(-1.0);
+  v->cs2 = RT;
+  v->c = sqrt(3.0 * RT);
+  for (int a = 0; a < 9; ++a) {
+    double ex, ey;
+    if (a == 0) {
+      ex = 0.0;
+      ey = 0.0;
+    } else if (a <= 4) {
+      double th = (a - 1) * pi / 2.0;
+      ex = cos(th);
+      ey = sin(th);
+    } else {
+      double th = (2 * a - 9) * pi / 4.0;
+      ex = sqrt(2.0) * cos(th);
+      ey = sqrt(2.0) * sin(th);
+    }
+    /* The nine velocities are c times points of the integer lattice; rounding
+     * removes the 1e-16 residue that cos(pi/2) and friends leave. */
+    v->xi[a][0] = v->c * (double)lround(ex);
+    v->xi[a][1] = v->c * (double)lround(ey);
+    v->w[a] = (a == 0) ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  for (int a = 0; a < 9; ++a) {
+    for (int b = 0; b < 9; ++b) {
+      if (v->xi[b][0] == -v->xi[a][0] && v->xi[b][1] == -v->xi[a][1]) v->opp[a] = b;
+      if (v->xi[b][0] == -v->xi[a][0] && v->xi[b][1] == v->xi[a][1]) v->mirx[a] = b;
+      if (v->xi[b][0] == v->xi[a][0] && v->xi[b][1] == -v->xi[a][1]) v->miry[a] = b;
+    }
+  }
+}
+
+/* Eq. equilibrium. */
+static void feq_of(const vset *v, double rho, double ux, double uy, double *feq) {
+  double usq = ux * ux + uy * uy;
+  for (int a = 0; a < 9; ++a) {
+    double eu = v->xi[a][0] * ux + v->xi[a][1] * uy;
+    feq[a] = v->w[a] * rho *
+             (1.0 + eu / v->cs2 + (eu * eu) / (2.0 * v->cs2 * v->cs2) -
+              usq / (2.0 * v->cs2));
+  }
+}
+
+/* Eqs. macro / macro_var. */
+static void moments_of(const vset *v, const double *f9, double *rho, double *ux,
+                       double *uy) {
+  double r = 0.0, jx = 0.0, jy = 0.0;
+  for (int a = 0; a < 9; ++a) {
+    r += f9[a];
+    jx += v->xi[a][0] * f9[a];
+    jy += v->xi[a][1] * f9[a];
+  }
+  *rho = r;
+  *ux = jx / r;
+  *uy = jy / r;
+}
+
+/* Omega(f) = (f_eq - f)/tau with f_eq from f's own moments (Eq. BGK_discrete). */
+static void omega_of(const vset *v, double tau, const double *f9, double *om) {
+  double rho, ux, uy, feq[9];
+  moments_of(v, f9, &rho, &ux, &uy);
+  feq_of(v, rho, ux, uy, feq);
+  for (int a = 0; a < 9; ++a) om[a] = (feq[a] - f9[a]) / tau;
+}
+
+int orc_d2q9(double RT, double *xi, double *w, int *opp) {
+  if (!(RT > 0.0) || !xi || !w || !opp) return ORC_EINVAL;
+  vset v;
+  make_vset(RT, &v);
+  for (int a = 0; a < 9; ++a) {
+    xi[2 * a] = v.xi[a][0];
+    xi[2 * a + 1] = v.xi[a][1];
+    w[a] = v.w[a];
+    opp[a] = v.opp[a];
+  }
+  return ORC_OK;
+}
+
+void orc_equilibrium(double RT, double rho, double ux, double uy, double *feq) {
+  vset v;
+  make_vset(RT, &v);
+  feq_of(&v, rho, ux, uy, feq);
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                               */
+/* ------------------------------------------------------------------ */
+
+int orc_faces_uniform(int n, double a, double b, double *out) {
+  if (n < 1 || !(b > a) || !out) return ORC_EINVAL;
+  for (int i = 0; i <= n; ++i) out[i] = a + (b - a) * (double)i / (double)n;
+  return ORC_OK;
+}
+
+int orc_faces_tanh(int n, double a, double b, double beta, double *out) {
+  if (n < 1 || !(b > a) || !(beta > 0.0) || !out) return ORC_EINVAL;
+  for (int i = 0; i <= n; ++i) {
+    double s = (double)i / (double)n;
+    out[i] = a + (b - a) * 0.5 * (1.0 + tanh(beta * (2.0 * s - 1.0)) / tanh(beta));
+  }
+  return ORC_OK;
+}
+
+int orc_faces_geometric(int n, double a, double d0, double ratio, double *out) {
+  if (n < 1 || !(d0 > 0.0) || !(ratio > 0.0) || !out) return ORC_EINVAL;
+  for (int i = 0; i <= n; ++i) {
+    if (ratio == 1.0)
+      out[i] = a + d0 * (double)i;
+    else
+      out[i] = a + d0 * (pow(ratio, (double)i) - 1.0) / (ratio - 1.0);
+  }
+  return ORC_OK;
+}
+
+int orc_dt_from_cfl(int nx, int ny, const double *xf, const double *yf, double RT,
+                    double cfl, double *dt) {
+  if (nx < 1 || ny < 1 || !xf || !yf || !(RT > 0.0) || !(cfl > 0.0) || !dt)
+    return ORC_EINVAL;
+  double dmin = INFINITY;
+  for (int i = 0; i < nx; ++i) {
+    double d = xf[i + 1] - xf[i];
+    if (!(d > 0.0)) return ORC_EINVAL;
+    if (d < dmin) dmin = d;
+  }
+  for (int j = 0; j < ny; ++j) {
+    double d = yf[j + 1] - yf[j];
+    if (!(d > 0.0)) return ORC_EINVAL;
+    if (d < dmin) dmin = d;
+  }
+  /* Eq. eq:cfl: |xi|_max = sqrt(6) c_s for D2Q9. */
+  *dt = cfl * dmin / (sqrt(6.0) * sqrt(RT));
+  return ORC_OK;
+}
+
+/* Cell centres with one ghost centre per side.  Non-periodic sides put the
+ * ghost centre at the mirror image of the first inner centre; periodic sides
+ * at the shifted image of the opposite inner centre. */
+typedef struct {
+  int nx, ny, per_x, per_y;
+  const double *xf, *yf;
+  double *xcb, *ycb; /* storage, index shifted by one */
+  double *xc, *yc;   /* xc[-1..nx], yc[-1..ny] */
+  const orc_bc_segment **segW, **segE, **segS, **segN; /* per boundary face */
+} geom;
+
+static void geom_free(geom *g) {
+  free(g->xcb);
+  free(g->ycb);
+  free((void *)g->segW);
+  free((void *)g->segE);
+  free((void *)g->segS);
+  free((void *)g->segN);
+  memset(g, 0, sizeof(*g));
+}
+
+static const orc_bc_segment *seg_at(const orc_problem *p, int side, double t) {
+  for (int k = 0; k < p->nbc[side]; ++k) {
+    const orc_bc_segment *s = &p->bc[side][k];
+    if (t >= s->s0 && t < s->s1) return s;
+  }
+  return NULL;
+}
+
+static int kind_valid(int k) { return k >= ORC_BC_PERIODIC && k <= ORC_BC_SYMMETRY; }
+
+static int geom_build(const orc_problem *p, geom *g) {
+  memset(g, 0, sizeof(*g));
+  if (!p || p->nx < 2 || p->ny < 2 || !p->xf || !p->yf) return ORC_EINVAL;
+  if (!(p->RT > 0.0) || !(p->tau > 0.0) || !(p->dt > 0.0)) return ORC_EINVAL;
+  if (p->scheme != ORC_DUGKS && p->scheme != ORC_BKG) return ORC_EINVAL;
+  for (int i = 0; i < p->nx; ++i)
+    if (!(p->xf[i + 1] > p->xf[i])) return ORC_EINVAL;
+  for (int j = 0; j < p->ny; ++j)
+    if (!(p->yf[j + 1] > p->yf[j])) return ORC_EINVAL;
+  int per[4];
+  for (int s = 0; s < 4; ++s) {
+    if (p->nbc[s] < 1 || !p->bc[s]) return ORC_EINVAL;
+    per[s] = 0;
+    for (int k = 0; k < p->nbc[s]; ++k) {
+      if (!kind_valid(p->bc[s][k].kind)) return ORC_EINVAL;
+      if (p->bc[s][k].kind == ORC_BC_PERIODIC) per[s] = 1;
+    }
+    if (per[s] && p->nbc[s] != 1) return ORC_EINVAL;
+  }
+  if (per[ORC_SIDE_W] != per[ORC_SIDE_E] || per[ORC_SIDE_S] != per[ORC_SIDE_N])
+    return ORC_EINVAL;
+  int nx = p->nx, ny = p->ny;
+  g->nx = nx;
+  g->ny = ny;
+  g->per_x = per[ORC_SIDE_W];
+  g->per_y = per[ORC_SIDE_S];
+  g->xf = p->xf;
+  g->yf = p->yf;
+  g->xcb = (double *)malloc(sizeof(double) * (nx + 2));
+  g->ycb = (double *)malloc(sizeof(double) * (ny + 2));
+  g->segW = (const orc_bc_segment **)calloc(ny, sizeof(void *));
+  g->segE = (const orc_bc_segment **)calloc(ny, sizeof(void *));
+  g->segS = (const orc_bc_segment **)calloc(nx, sizeof(void *));
+  g->segN = (const orc_bc_segment **)calloc(nx, sizeof(void *));
+  if (!g->xcb || !g->ycb || !g->segW || !g->segE || !g->segS || !g->segN) {
+    geom_free(g);
+    return ORC_EINVAL;
+  }
+  g->xc = g->xcb + 1;
+  g->yc = g->ycb + 1;
+  for (int i = 0; i < nx; ++i) g->xc[i] = 0.5 * (p->xf[i] + p->xf[i + 1]);
+  for (int j = 0; j < ny; ++j) g->yc[j] = 0.5 * (p->yf[j] + p->yf[j + 1]);
+  double Lx = p->xf[nx] - p->xf[0], Ly = p->yf[ny] - p->yf[0];
+  if (g->per_x) {
+    g->xc[-1] = g->xc[nx - 1] - Lx;
+    g->xc[nx] = g->xc[0] + Lx;
+  } else {
+    g->xc[-1] = 2.0 * p->xf[0] - g->xc[0];
+    g->xc[nx] = 2.0 * p->xf[nx] - g->xc[nx - 1];
+  }
+  if (g->per_y) {
+    g->yc[-1] = g->yc[ny - 1] - Ly;
+    g->yc[ny] = g->yc[0] + Ly;
+  } else {
+    g->yc[-1] = 2.0 * p->yf[0] - g->yc[0];
+    g->yc[ny] = 2.0 * p->yf[ny] - g->yc[ny - 1];
+  }
+  for (int j = 0; j < ny; ++j) {
+    g->segW[j] = seg_at(p, ORC_SIDE_W, g->yc[j]);
+    g->segE[j] = seg_at(p, ORC_SIDE_E, g->yc[j]);
+    if (g->per_x) g->segW[j] = g->segE[j] = NULL;
+    else if (!g->segW[j] || !g->segE[j]) {
+      geom_free(g);
+      return ORC_EINVAL;
+    }
+  }
+  for (int i = 0; i < nx; ++i) {
+    g->segS[i] = seg_at(p, ORC_SIDE_S, g->xc[i]);
+    g->segN[i] = seg_at(p, ORC_SIDE_N, g->xc[i]);
+    if (g->per_y) g->segS[i] = g->segN[i] = NULL;
+    else if (!g->segS[i] || !g->segN[i]) {
+      geom_free(g);
+      return ORC_EINVAL;
+    }
+    if (!g->per_y && (g->segS[i]->kind == ORC_BC_PERIODIC ||
+                      g->segN[i]->kind == ORC_BC_PERIODIC)) {
+      geom_free(g);
+      return ORC_EINVAL;
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ghost layer (Sec 2.5 and the inflow/outflow/symmetry of Sec 3.3)   */
+/* ------------------------------------------------------------------ */
+
+/* Padded array of 9 fields over i = -1..nx, j = -1..ny. */
+#define PIDX(g, i, j) (((j) + 1) * ((g)->nx + 2) + ((i) + 1))
+
+static void ghost_rule(const vset *v, const orc_bc_segment *s, double e, const int *mir,
+                       const double *p1, const double *p2, double *pg) {
+  switch (s->kind) {
+    case ORC_BC_WALL_BOUNCEBACK:
+    case ORC_BC_WALL_DIFFUSE:
+      /* linear extrapolation from the first two inner centres */
+      for (int a = 0; a < 9; ++a) pg[a] = p1[a] + e * (p1[a] - p2[a]);
+      break;
+    case ORC_BC_INFLOW_EQ:
+      feq_of(v, s->rho, s->ux, s->uy, pg);
+      break;
+    case ORC_BC_OUTFLOW_ZG:
+      for (int a = 0; a < 9; ++a) pg[a] = p1[a];
+      break;
+    case ORC_BC_SYMMETRY:
+      for (int a = 0; a < 9; ++a) pg[a] = p1[mir[a]];
+      break;
+    default:
+      break;
+  }
+}
+
+static void fill_ghosts(const vset *v, const geom *g, double *P) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t plane = (size_t)(nx + 2) * (ny + 2);
+  double p1[9], p2[9], pg[9];
+  /* extrapolation factors e = (x_g - x_1)/(x_1 - x_2) per side */
+  const double eW = (g->xc[-1] - g->xc[0]) / (g->xc[0] - g->xc[1]);
+  const double eE = (g->xc[nx] - g->xc[nx - 1]) / (g->xc[nx - 1] - g->xc[nx - 2]);
+  const double eS = (g->yc[-1] - g->yc[0]) / (g->yc[0] - g->yc[1]);
+  const double eN = (g->yc[ny] - g->yc[ny - 1]) / (g->yc[ny - 1] - g->yc[ny - 2]);
+
+  /* x sides first, interior rows only */
+  for (int j = 0; j < ny; ++j) {
+    for (int side = 0; side < 2; ++side) {
+      int ig = side == 0 ? -1 : nx;
+      int i1 = side == 0 ? 0 : nx - 1;
+      int i2 = side == 0 ? 1 : nx - 2;
+      if (g->per_x) {
+        int src = side == 0 ? nx - 1 : 0;
+        for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, ig, j)] = P[a * plane + PIDX(g, src, j)];
+        continue;
+      }
+      for (int a = 0; a < 9; ++a) {
+        p1[a] = P[a * plane + PIDX(g, i1, j)];
+        p2[a] = P[a * plane + PIDX(g, i2, j)];
+      }
+      const orc_bc_segment *s = side == 0 ? g->segW[j] : g->segE[j];
+      ghost_rule(v, s, side == 0 ? eW : eE, v->mirx, p1, p2, pg);
+      for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, ig, j)] = pg[a];
+    }
+  }
+  /* then y sides over the full padded width (corners included) */
+  for (int i = -1; i <= nx; ++i) {
+    int ic = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+    for (int side = 0; side < 2; ++side) {
+      int jg = side == 0 ? -1 : ny;
+      int j1 = side == 0 ? 0 : ny - 1;
+      int j2 = side == 0 ? 1 : ny - 2;
+      if (g->per_y) {
+        int src = side == 0 ? ny - 1 : 0;
+        for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = P[a * plane + PIDX(g, i, src)];
+        continue;
+      }
+      for (int a = 0; a < 9; ++a) {
+        p1[a] = P[a * plane + PIDX(g, i, j1)];
+        p2[a] = P[a * plane + PIDX(g, i, j2)];
+      }
+      const orc_bc_segment *s = side == 0 ? g->segS[ic] : g->segN[ic];
+      ghost_rule(v, s, side == 0 ? eS : eN, v->miry, p1, p2, pg);
+      for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = pg[a];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Face values                                                        */
+/* ------------------------------------------------------------------ */
+
+/* phi(x_b - h xi) at the x-face i (between cells i-1 and i), row j. */
+static void recon_xface(const vset *v, const geom *g, const double *P, int i, int j,
+                        double h, double *out) {
+  const size_t plane = (size_t)(g->nx + 2) * (g->ny + 2);
+  double xl = g->xc[i - 1], xr = g->xc[i], xb = g->xf[i];
+  double th = (xb - xl) / (xr - xl);
+  double ylo = g->yc[j - 1], yhi = g->yc[j + 1];
+  for (int a = 0; a < 9; ++a) {
+    const double *Pa = P + a * plane;
+    double pl = Pa[PIDX(g, i - 1, j)], pr = Pa[PIDX(g, i, j)];
+    double gl = (Pa[PIDX(g, i - 1, j + 1)] - Pa[PIDX(g, i - 1, j - 1)]) / (yhi - ylo);
+    double gr = (Pa[PIDX(g, i, j + 1)] - Pa[PIDX(g, i, j - 1)]) / (yhi - ylo);
+    double value = (1.0 - th) * pl + th * pr;
+    double slope_n = (pr - pl) / (xr - xl);
+    double slope_t = (1.0 - th) * gl + th * gr;
+    out[a] = value - h * (v->xi[a][0] * slope_n + v->xi[a][1] * slope_t);
+  }
+}
+
+/* phi(x_b - h xi) at the y-face j (between rows j-1 and j), column i. */
+static void recon_yface(const vset *v, const geom *g, const double *P, int i, int j,
+                        double h, double *out) {
+  const size_t plane = (size_t)(g->nx + 2) * (g->ny + 2);
+  double yl = g->yc[j - 1], yr = g->yc[j], yb = g->yf[j];
+  double th = (yb - yl) / (yr - yl);
+  double xlo = g->xc[i - 1], xhi = g->xc[i + 1];
+  for (int a = 0; a < 9; ++a) {
+    const double *Pa = P + a * plane;
+    double pl = Pa[PIDX(g, i, j - 1)], pr = Pa[PIDX(g, i, j)];
+    double gl = (Pa[PIDX(g, i + 1, j - 1)] - Pa[PIDX(g, i - 1, j - 1)]) / (xhi - xlo);
+    double gr = (Pa[PIDX(g, i + 1, j)] - Pa[PIDX(g, i - 1, j)]) / (xhi - xlo);
+    double value = (1.0 - th) * pl + th * pr;
+    double slope_n = (pr - pl) / (yr - yl);
+    double slope_t = (1.0 - th) * gl + th * gr;
+    out[a] = value - h * (v->xi[a][0] * slope_t + v->xi[a][1] * slope_n);
+  }
+}
+
+/* Sec 2.5 at a boundary face; n = outward normal of the fluid domain. */
+static void face_bc(const vset *v, const orc_bc_segment *s, double nxo, double nyo,
+                    double *val) {
+  double orig[9];
+  memcpy(orig, val, sizeof(orig));
+  switch (s->kind) {
+    case ORC_BC_WALL_BOUNCEBACK:
+      for (int a = 0; a < 9; ++a) {
+        double xn = v->xi[a][0] * nxo + v->xi[a][1] * nyo;
+        if (xn > 0.0) {
+          double xu = v->xi[a][0] * s->ux + v->xi[a][1] * s->uy;
+          val[v->opp[a]] = orig[a] - 2.0 * v->w[a] * xu / v->cs2;
+        }
+      }
+      break;
+    case ORC_BC_WALL_DIFFUSE: {
+      double f1[9], num = 0.0, den = 0.0;
+      feq_of(v, 1.0, s->ux, s->uy, f1);
+      for (int a = 0; a < 9; ++a) {
+        double xn = v->xi[a][0] * nxo + v->xi[a][1] * nyo;
+        if (xn > 0.0) num += xn * orig[a];
+        if (xn < 0.0) den += -xn * f1[a];
+      }
+      double rw = num / den;
+      for (int a = 0; a < 9; ++a) {
+        double xn = v->xi[a][0] * nxo + v->xi[a][1] * nyo;
+        if (xn < 0.0) val[a] = rw * f1[a];
+      }
+      break;
+    }
+    case ORC_BC_INFLOW_EQ:
+      feq_of(v, s->rho, s->ux, s->uy, val);
+      break;
+    default:
+      break;
+  }
+}
+
+/* DUGKS: from f_bar at the face to the original f (Eq. eq_trans_2 inverted,
+ * with the face moments of f_bar).  BKG: the face value is f already (Eq. bkg_fb). */
+static void face_to_f(const vset *v, const orc_problem *p, double *val) {
+  if (p->scheme != ORC_DUGKS) return;
+  const double h = 0.5 * p->dt, tau = p->tau;
+  double rho, ux, uy, fe[9];
+  moments_of(v, val, &rho, &ux, &uy);
+  feq_of(v, rho, ux, uy, fe);
+  for (int a = 0; a < 9; ++a) val[a] = (2.0 * tau * val[a] + h * fe[a]) / (2.0 * tau + h);
+}
+
+/* ------------------------------------------------------------------ */
+/* The explicit step                                                  */
+/* ------------------------------------------------------------------ */
+
+static int step_once(const orc_problem *p, const vset *v, const geom *g, double *ft,
+                     double *P, double *TP, double *FX, double *FY) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t n = (size_t)nx * ny, plane = (size_t)(nx + 2) * (ny + 2);
+  const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
+  double f9[9], fe[9], rho, ux, uy, val[9];
+
+  /* 1-2: cell moments, equilibrium, phi and f_tilde^+ */
+  for (int j = 0; j < ny; ++j) {
+    for (int i = 0; i < nx; ++i) {
+      size_t k = (size_t)j * nx + i;
+      for (int a = 0; a < 9; ++a) f9[a] = ft[a * n + k];
+      moments_of(v, f9, &rho, &ux, &uy);
+      feq_of(v, rho, ux, uy, fe);
+      for (int a = 0; a < 9; ++a) {
+        double tplus = ((2.0 * tau - dt) * f9[a] + 2.0 * dt * fe[a]) / (2.0 * tau + dt);
+        double phi;
+        if (p->scheme == ORC_DUGKS)
+          phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);
+        else
+          phi = tplus;
+        TP[a * n + k] = tplus;
+        P[a * plane + PIDX(g, i, j)] = phi;
+      }
+    }
+  }
+  /* 3: ghost layer */
+  fill_ghosts(v, g, P);
+
+  /* 4-6: x-faces i = 0..nx, rows 0..ny-1 */
+  for (int j = 0; j < ny; ++j) {
+    for (int i = 0; i <= nx; ++i) {
+      recon_xface(v, g, P, i, j, h, val);
+      if (!g->per_x && i == 0) face_bc(v, g->segW[j], -1.0, 0.0, val);
+      if (!g->per_x && i == nx) face_bc(v, g->segE[j], 1.0, 0.0, val);
+      face_to_f(v, p, val);
+      for (int a = 0; a < 9; ++a) FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i] = val[a];
+    }
+  }
+  /* y-faces j = 0..ny, columns 0..nx-1 */
+  for (int j = 0; j <= ny; ++j) {
+    for (int i = 0; i < nx; ++i) {
+      recon_yface(v, g, P, i, j, h, val);
+      if (!g->per_y && j == 0) face_bc(v, g->segS[i], 0.0, -1.0, val);
+      if (!g->per_y && j == ny) face_bc(v, g->segN[i], 0.0, 1.0, val);
+      face_to_f(v, p, val);
+      for (int a = 0; a < 9; ++a) FY[(size_t)a * nx * (ny + 1) + (size_t)j * nx + i] = val[a];
+    }
+  }
+  /* 7: f_tilde^{n+1} = f_tilde^+ - dt/|V| sum_faces (xi . n_out) A f_face */
+  for (int j = 0; j < ny; ++j) {
+    double dy = g->yf[j + 1] - g->yf[j];
+    for (int i = 0; i < nx; ++i) {
+      double dx = g->xf[i + 1] - g->xf[i];
+      double vol = dx * dy;
+      size_t k = (size_t)j * nx + i;
+      for (int a = 0; a < 9; ++a) {
+        double fw = FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i];
+        double fE = FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i + 1];
+        double fs = FY[(size_t)a * nx * (ny + 1) + (size_t)j * nx + i];
+        double fn = FY[(size_t)a * nx * (ny + 1) + (size_t)(j + 1) * nx + i];
+        double out_flux = v->xi[a][0] * dy * (fE - fw) + v->xi[a][1] * dx * (fn - fs);
+        ft[a * n + k] = TP[a * n + k] - dt / vol * out_flux;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+int orc_step(const orc_problem *p, double *f_tilde, long long nsteps) {
+  if (!f_tilde || nsteps < 0) return ORC_EINVAL;
+  geom g;
+  int rc = geom_build(p, &g);
+  if (rc) return rc;
+  vset v;
+  make_vset(p->RT, &v);
+  const int nx = p->nx, ny = p->ny;
+  double *P = (double *)calloc((size_t)9 * (nx + 2) * (ny + 2), sizeof(double));
+  double *TP = (double *)calloc((size_t)9 * nx * ny, sizeof(double));
+  double *FX = (double *)calloc((size_t)9 * (nx + 1) * ny, sizeof(double));
+  double *FY = (double *)calloc((size_t)9 * nx * (ny + 1), sizeof(double));
+  if (!P || !TP || !FX || !FY) rc = ORC_EINVAL;
+  for (long long s = 0; s < nsteps && !rc; ++s) rc = step_once(p, &v, &g, f_tilde, P, TP, FX, FY);
+  free(P);
+  free(TP);
+  free(FX);
+  free(FY);
+  geom_free(&g);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* BKG, finite-difference Lax-Wendroff form (Eqs. bkgfd, central_schemes) */
+/* ------------------------------------------------------------------ */
+
+static int uniform_spacing(const double *f, int n, double *d) {
+  double d0 = f[1] - f[0];
+  for (int i = 1; i < n; ++i)
+    if (fabs((f[i + 1] - f[i]) - d0) > 1e-12 * fabs(d0)) return 0;
+  *d = (f[n] - f[0]) / (double)n;
+  return 1;
+}
+
+static void lw_fd_periodic(const vset *v, int nx, int ny, double dx1, double dx2,
+                           double dt, const double *phi, double *out) {
+  const size_t n = (size_t)nx * ny;
+  for (int a = 0; a < 9; ++a) {
+    const double *F = phi + a * n;
+    double x1 = v->xi[a][0], x2 = v->xi[a][1];
+    for (int m = 0; m < ny; ++m) {
+      int mp = (m + 1) % ny, mm = (m + ny - 1) % ny;
+      for (int l = 0; l < nx; ++l) {
+        int lp = (l + 1) % nx, lm = (l + nx - 1) % nx;
+        double c = F[(size_t)m * nx + l];
+        double d1 = (F[(size_t)m * nx + lp] - F[(size_t)m * nx + lm]) / (2.0 * dx1);
+        double d2 = (F[(size_t)mp * nx + l] - F[(size_t)mm * nx + l]) / (2.0 * dx2);
+        double d11 = (F[(size_t)m * nx + lp] + F[(size_t)m * nx + lm] - 2.0 * c) / (dx1 * dx1);
+        double d22 = (F[(size_t)mp * nx + l] + F[(size_t)mm * nx + l] - 2.0 * c) / (dx2 * dx2);
+        double d12 = (F[(size_t)mp * nx + lp] - F[(size_t)mp * nx + lm] -
+                      F[(size_t)mm * nx + lp] + F[(size_t)mm * nx + lm]) /
+                     (4.0 * dx1 * dx2);
+        out[a * n + (size_t)m * nx + l] =
+            c - dt * (x1 * d1 + x2 * d2) +
+            0.5 * dt * dt * (x1 * x1 * d11 + 2.0 * x1 * x2 * d12 + x2 * x2 * d22);
+      }
+    }
+  }
+}
+
+int orc_step_bkg_fd(const orc_problem *p, double *f_tilde, long long nsteps) {
+  if (!f_tilde || nsteps < 0) return ORC_EINVAL;
+  geom g;
+  int rc = geom_build(p, &g);
+  if (rc) return rc;
+  double dx1, dx2;
+  if (!g.per_x || !g.per_y || !uniform_spacing(p->xf, p->nx, &dx1) ||
+      !uniform_spacing(p->yf, p->ny, &dx2)) {
+    geom_free(&g);
+    return ORC_EINVAL;
+  }
+  vset v;
+  make_vset(p->RT, &v);
+  const int nx = p->nx, ny = p->ny;
+  const size_t n = (size_t)nx * ny;
+  const double dt = p->dt, tau = p->tau;
+  double *phi = (double *)malloc(sizeof(double) * 9 * n);
+  if (!phi) rc = ORC_EINVAL;
+  for (long long s = 0; s < nsteps && !rc; ++s) {
+    for (size_t k = 0; k < n; ++k) {
+      double f9[9], fe[9], rho, ux, uy;
+      for (int a = 0; a < 9; ++a) f9[a] = f_tilde[a * n + k];
+      moments_of(&v, f9, &rho, &ux, &uy);
+      feq_of(&v, rho, ux, uy, fe);
+      /* Eq. bkg_collision: the collision step gives f_tilde^+ */
+      for (int a = 0; a < 9; ++a)
+        phi[a * n + k] = ((2.0 * tau - dt) * f9[a] + 2.0 * dt * fe[a]) / (2.0 * tau + dt);
+    }
+    lw_fd_periodic(&v, nx, ny, dx1, dx2, dt, phi, f_tilde);
+  }
+  free(phi);
+  geom_free(&g);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Brute force from the implicit forms                                */
+/* ------------------------------------------------------------------ */
+
+/* Solve out - k Omega(out) = rhs for out by the damped fixed point
+ * out <- (rhs + (k/tau) f_eq(out)) / (1 + k/tau). */
+static int solve_implicit(const vset *v, double tau, double k, const double *rhs,
+                          double *out) {
+  double scale = 0.0, om[9];
+  for (int a = 0; a < 9; ++a) {
+    out[a] = rhs[a];
+    if (fabs(rhs[a]) > scale) scale = fabs(rhs[a]);
+  }
+  for (int it = 0; it < 200; ++it) {
+    double rho, ux, uy, fe[9];
+    moments_of(v, out, &rho, &ux, &uy);
+    feq_of(v, rho, ux, uy, fe);
+    for (int a = 0; a < 9; ++a) out[a] = (rhs[a] + (k / tau) * fe[a]) / (1.0 + k / tau);
+    omega_of(v, tau, out, om);
+    double res = 0.0;
+    for (int a = 0; a < 9; ++a) {
+      double r = fabs(out[a] - k * om[a] - rhs[a]);
+      if (r > res) res = r;
+    }
+    /* rounding level of the residual expression itself */
+    if (res <= 8.0 * 2.220446049250313e-16 * (1.0 + k / tau) * scale) return ORC_OK;
+  }
+  return ORC_EINVAL;
+}
+
+int orc_tilde_from_f(const orc_problem *p, const double *f, double *f_tilde) {
+  if (!p || !f || !f_tilde || p->nx < 1 || p->ny < 1 || !(p->tau > 0.0)) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  for (size_t k = 0; k < n; ++k) {
+    double f9[9], om[9];
+    for (int a = 0; a < 9; ++a) f9[a] = f[a * n + k];
+    omega_of(&v, p->tau, f9, om);
+    for (int a = 0; a < 9; ++a) f_tilde[a * n + k] = f9[a] - 0.5 * p->dt * om[a];
+  }
+  return ORC_OK;
+}
+
+static int implicit_dugks_once(const orc_problem *p, const vset *v, const geom *g,
+                               double *f, double *P, double *TP, double *FX, double *FY) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t n = (size_t)nx * ny, plane = (size_t)(nx + 2) * (ny + 2);
+  const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
+  double f9[9], om[9], val[9], F[9];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = (size_t)j * nx + i;
+      for (int a = 0; a < 9; ++a) f9[a] = f[a * n + k];
+      omega_of(v, tau, f9, om);
+      for (int a = 0; a < 9; ++a) {
+        P[a * plane + PIDX(g, i, j)] = f9[a] + 0.5 * h * om[a]; /* f_bar^+ */
+        TP[a * n + k] = f9[a] + 0.5 * dt * om[a];                /* f + dt/2 Omega */
+      }
+    }
+  fill_ghosts(v, g, P);
+  /* Eq. eq_charraw along the characteristic: F - h/2 Omega(F) = f_bar^+(foot) */
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i <= nx; ++i) {
+      recon_xface(v, g, P, i, j, h, val);
+      if (solve_implicit(v, tau, 0.5 * h, val, F)) return ORC_EINVAL;
+      for (int a = 0; a < 9; ++a) FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i] = F[a];
+    }
+  for (int j = 0; j <= ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      recon_yface(v, g, P, i, j, h, val);
+      if (solve_implicit(v, tau, 0.5 * h, val, F)) return ORC_EINVAL;
+      for (int a = 0; a < 9; ++a) FY[(size_t)a * nx * (ny + 1) + (size_t)j * nx + i] = F[a];
+    }
+  /* Eq. eq_raw: f^{n+1} - dt/2 Omega(f^{n+1}) = f^n + dt/2 Omega(f^n) + dt/|V| F_in */
+  for (int j = 0; j < ny; ++j) {
+    double dy = g->yf[j + 1] - g->yf[j];
+    for (int i = 0; i < nx; ++i) {
+      double dx = g->xf[i + 1] - g->xf[i];
+      size_t k = (size_t)j * nx + i;
+      double rhs[9];
+      for (int a = 0; a < 9; ++a) {
+        double fw = FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i];
+        double fE = FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i + 1];
+        double fs = FY[(size_t)a * nx * (ny + 1) + (size_t)j * nx + i];
+        double fn = FY[(size_t)a * nx * (ny + 1) + (size_t)(j + 1) * nx + i];
+        double flux_in = -(v->xi[a][0] * dy * (fE - fw) + v->xi[a][1] * dx * (fn - fs));
+        rhs[a] = TP[a * n + k] + dt / (dx * dy) * flux_in;
+      }
+      if (solve_implicit(v, tau, 0.5 * dt, rhs, F)) return ORC_EINVAL;
+      for (int a = 0; a < 9; ++a) f[a * n + k] = F[a];
+    }
+  }
+  return ORC_OK;
+}
+
+static int implicit_bkg_once(const orc_problem *p, const vset *v, const geom *g,
+                             double dx1, double dx2, double *f, double *ts, double *tn) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t n = (size_t)nx * ny;
+  const double dt = p->dt, tau = p->tau;
+  double f9[9], om[9], rhs[9], fs[9];
+  for (size_t k = 0; k < n; ++k) {
+    for (int a = 0; a < 9; ++a) f9[a] = f[a * n + k];
+    /* Eq. splic_c: f* - dt/2 Omega(f*) = f^n + dt/2 Omega(f^n) */
+    omega_of(v, tau, f9, om);
+    for (int a = 0; a < 9; ++a) rhs[a] = f9[a] + 0.5 * dt * om[a];
+    if (solve_implicit(v, tau, 0.5 * dt, rhs, fs)) return ORC_EINVAL;
+    /* f_tilde* = f* - dt/2 Omega(f*) */
+    omega_of(v, tau, fs, om);
+    for (int a = 0; a < 9; ++a) ts[a * n + k] = fs[a] - 0.5 * dt * om[a];
+  }
+  /* Eq. split_b by Lax-Wendroff (Eq. bkgfd) */
+  lw_fd_periodic(v, nx, ny, dx1, dx2, dt, ts, tn);
+  /* back to the original distribution: f - dt/2 Omega(f) = f_tilde */
+  for (size_t k = 0; k < n; ++k) {
+    for (int a = 0; a < 9; ++a) rhs[a] = tn[a * n + k];
+    if (solve_implicit(v, tau, 0.5 * dt, rhs, fs)) return ORC_EINVAL;
+    for (int a = 0; a < 9; ++a) f[a * n + k] = fs[a];
+  }
+  return ORC_OK;
+}
+
+int orc_step_implicit(const orc_problem *p, double *f, long long nsteps) {
+  if (!f || nsteps < 0) return ORC_EINVAL;
+  geom g;
+  int rc = geom_build(p, &g);
+  if (rc) return rc;
+  if (!g.per_x || !g.per_y) {
+    geom_free(&g);
+    return ORC_EINVAL;
+  }
+  vset v;
+  make_vset(p->RT, &v);
+  const int nx = p->nx, ny = p->ny;
+  const size_t n = (size_t)nx * ny;
+  if (p->scheme == ORC_DUGKS) {
+    double *P = (double *)calloc((size_t)9 * (nx + 2) * (ny + 2), sizeof(double));
+    double *TP = (double *)calloc(9 * n, sizeof(double));
+    double *FX = (double *)calloc((size_t)9 * (nx + 1) * ny, sizeof(double));
+    double *FY = (double *)calloc((size_t)9 * nx * (ny + 1), sizeof(double));
+    if (!P || !TP || !FX || !FY) rc = ORC_EINVAL;
+    for (long long s = 0; s < nsteps && !rc; ++s)
+      rc = implicit_dugks_once(p, &v, &g, f, P, TP, FX, FY);
+    free(P);
+    free(TP);
+    free(FX);
+    free(FY);
+  } else {
+    double dx1, dx2;
+    if (!uniform_spacing(p->xf, nx, &dx1) || !uniform_spacing(p->yf, ny, &dx2)) {
+      geom_free(&g);
+      return ORC_EINVAL;
+    }
+    double *ts = (double *)malloc(sizeof(double) * 9 * n);
+    double *tn = (double *)malloc(sizeof(double) * 9 * n);
+    if (!ts || !tn) rc = ORC_EINVAL;
+    for (long long s = 0; s < nsteps && !rc; ++s)
+      rc = implicit_bkg_once(p, &v, &g, dx1, dx2, f, ts, tn);
+    free(ts);
+    free(tn);
+  }
+  geom_free(&g);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial states                                                     */
+/* ------------------------------------------------------------------ */
+
+int orc_init_equilibrium(const orc_problem *p, const double *rho, const double *ux,
+                         const double *uy, double *f_tilde) {
+  if (!p || !rho || !ux || !uy || !f_tilde || p->nx < 1 || p->ny < 1) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  double fe[9];
+  for (size_t k = 0; k < n; ++k) {
+    feq_of(&v, rho[k], ux[k], uy[k], fe);
+    for (int a = 0; a < 9; ++a) f_tilde[a * n + k] = fe[a];
+  }
+  return ORC_OK;
+}
+
+int orc_init_chapman_enskog(const orc_problem *p, const double *rho, const double *ux,
+                            const double *uy, const double *const *d, double *f_tilde) {
+  if (!p || !rho || !ux || !uy || !d || !f_tilde || p->nx < 1 || p->ny < 1) return ORC_EINVAL;
+  for (int q = 0; q < 9; ++q)
+    if (!d[q]) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  const double cs2 = v.cs2, tau = p->tau, dt = p->dt;
+  for (size_t k = 0; k < n; ++k) {
+    double r = rho[k], u = ux[k], w = uy[k];
+    double fe[9], f9[9], om[9];
+    feq_of(&v, r, u, w, fe);
+    for (int a = 0; a < 9; ++a) {
+      double cx = v.xi[a][0], cy = v.xi[a][1];
+      double eu = cx * u + cy * w;
+      /* partial derivatives of Eq. equilibrium with respect to rho, u_x, u_y */
+      double d_rho = fe[a] / r;
+      double d_ux = v.w[a] * r * (cx / cs2 + eu * cx / (cs2 * cs2) - u / cs2);
+      double d_uy = v.w[a] * r * (cy / cs2 + eu * cy / (cs2 * cs2) - w / cs2);
+      double dt_feq = d_rho * d[0][k] + d_ux * d[1][k] + d_uy * d[2][k];
+      double dx_feq = d_rho * d[3][k] + d_ux * d[4][k] + d_uy * d[5][k];
+      double dy_feq = d_rho * d[6][k] + d_ux * d[7][k] + d_uy * d[8][k];
+      f9[a] = fe[a] - tau * (dt_feq + cx * dx_feq + cy * dy_feq);
+    }
+    omega_of(&v, tau, f9, om);
+    for (int a = 0; a < 9; ++a) f_tilde[a * n + k] = f9[a] - 0.5 * dt * om[a];
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics                                                        */
+/* ------------------------------------------------------------------ */
+
+int orc_moments(const orc_problem *p, const double *f_tilde, double *rho, double *ux,
+                double *uy) {
+  if (!p || !f_tilde || !rho || !ux || !uy || p->nx < 1 || p->ny < 1) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  for (size_t k = 0; k < n; ++k) {
+    double f9[9];
+    for (int a = 0; a < 9; ++a) f9[a] = f_tilde[a * n + k];
+    moments_of(&v, f9, &rho[k], &ux[k], &uy[k]);
+  }
+  return ORC_OK;
+}
+
+int orc_conserved(const orc_problem *p, const double *f_tilde, double *out) {
+  if (!p || !f_tilde || !out || p->nx < 1 || p->ny < 1 || !p->xf || !p->yf) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  double m = 0.0, jx = 0.0, jy = 0.0;
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i) {
+      size_t k = (size_t)j * p->nx + i;
+      double vol = (p->xf[i + 1] - p->xf[i]) * (p->yf[j + 1] - p->yf[j]);
+      for (int a = 0; a < 9; ++a) {
+        double fa = f_tilde[a * n + k];
+        m += fa * vol;
+        jx += v.xi[a][0] * fa * vol;
+        jy += v.xi[a][1] * fa * vol;
+      }
+    }
+  out[0] = m;
+  out[1] = jx;
+  out[2] = jy;
+  return ORC_OK;
+}
+
+int orc_l2_error_u(const orc_problem *p, const double *f_tilde, const double *ua,
+                   const double *va, double *eu) {
+  if (!p || !f_tilde || !ua || !va || !eu || p->nx < 1 || p->ny < 1) return ORC_EINVAL;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  double num = 0.0, den = 0.0;
+  for (size_t k = 0; k < n; ++k) {
+    double f9[9], rho, ux, uy;
+    for (int a = 0; a < 9; ++a) f9[a] = f_tilde[a * n + k];
+    moments_of(&v, f9, &rho, &ux, &uy);
+    num += (ux - ua[k]) * (ux - ua[k]) + (uy - va[k]) * (uy - va[k]);
+    den += ua[k] * ua[k] + va[k] * va[k];
+  }
+  *eu = sqrt(num) / sqrt(den);
+  return ORC_OK;
+}

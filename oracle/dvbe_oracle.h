@@ -1,0 +1,127 @@
+/*
+ * Plain FP64 CPU oracle for the D2Q9 DUGKS / BKG finite-volume step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library
+ * against the paper (Zhu, Wang, Guo, "Performance evaluation of the general
+ * characteristics based off-lattice Boltzmann and DUGKS methods ...",
+ * arXiv 1511.00242).  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference leg may load it.  It shares no code, header,
+ * table or constant with the CUDA path.
+ *
+ * Every routine is written for clarity: nested loops, explicit ghost and
+ * face arrays, no blocking, no fusion.  Section / equation references are to
+ * the paper:
+ *   Sec 2.1  D2Q9 velocity set, equilibrium, moments, nu = tau RT
+ *   Sec 2.2  DUGKS (Eqs. dugks_fv, eq_raw, eq_update, eq_flux, eq_charraw,
+ *            eq_trans_2, eq_char, eq:cfl)
+ *   Sec 2.3  BKG (Eqs. split_a/b, splic_c, bkg_collision, bkgfd,
+ *            central_schemes, lwfv, G, bkg_fb, bkg_fv, f_left)
+ *   Sec 2.5  no-slip wall: ghost cells + half-way bounce-back
+ *   Sec 3.1  Taylor-Green set-up, Chapman-Enskog initial state, E_u
+ *
+ * Parity pins for each function are listed in tests/test_oracle_pins.py.
+ * Functions without a pin from the paper or from mathematics say
+ * "parity unpinned" below:
+ *   - the diffuse-reflection wall (the paper has none; only its zero
+ *     normal mass flux is pinned),
+ *   - the corner-ghost fill order (the paper is silent).
+ */
+#ifndef DVBE_ORACLE_H
+#define DVBE_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_DUGKS = 0, ORC_BKG = 1 };
+
+enum {
+  ORC_BC_PERIODIC = 0,
+  ORC_BC_WALL_BOUNCEBACK = 1,
+  ORC_BC_WALL_DIFFUSE = 2,
+  ORC_BC_INFLOW_EQ = 3,
+  ORC_BC_OUTFLOW_ZG = 4,
+  ORC_BC_SYMMETRY = 5
+};
+
+enum { ORC_SIDE_W = 0, ORC_SIDE_E = 1, ORC_SIDE_S = 2, ORC_SIDE_N = 3 };
+
+/* One boundary segment on a side: faces whose centre coordinate along the
+ * side lies in [s0, s1) take this condition.  (rho, ux, uy) is the wall
+ * velocity (walls) or the free-stream state (inflow). */
+typedef struct {
+  int kind;
+  double s0, s1;
+  double rho, ux, uy;
+} orc_bc_segment;
+
+/* The problem as the paper states it: mesh (face coordinates of a tensor
+ * mesh), velocity model (RT), relaxation time tau, time step dt, scheme and
+ * boundary conditions.  Arrays are borrowed, never freed. */
+typedef struct {
+  int nx, ny;
+  const double *xf; /* nx+1 x-face coordinates, strictly increasing */
+  const double *yf; /* ny+1 y-face coordinates, strictly increasing */
+  double RT, tau, dt;
+  int scheme;       /* ORC_DUGKS or ORC_BKG */
+  int nbc[4];       /* segments per side, W E S N */
+  const orc_bc_segment *bc[4];
+} orc_problem;
+
+/* Status codes: 0 ok, <0 bad argument. */
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+
+/* Sec 2.1: velocity set xi[9][2], weights w[9], reverse directions opp[9]. */
+int orc_d2q9(double RT, double *xi, double *w, int *opp);
+/* Sec 2.1, Eq. equilibrium. */
+void orc_equilibrium(double RT, double rho, double ux, double uy, double *feq);
+
+/* Mesh helpers (face coordinates). */
+int orc_faces_uniform(int n, double a, double b, double *out);
+int orc_faces_tanh(int n, double a, double b, double beta, double *out);
+int orc_faces_geometric(int n, double a, double d0, double ratio, double *out);
+/* Eq. eq:cfl with dx the smallest cell width in either direction. */
+int orc_dt_from_cfl(int nx, int ny, const double *xf, const double *yf,
+                    double RT, double cfl, double *dt);
+
+/* Initial states.  Host arrays: fields [ny][nx], f_tilde [9][ny][nx]. */
+int orc_init_equilibrium(const orc_problem *p, const double *rho,
+                         const double *ux, const double *uy, double *f_tilde);
+/* Sec 3.1: f = f_eq - tau (d_t f_eq + xi . grad f_eq), with the derivative of
+ * f_eq taken through (rho, u) by the chain rule from the supplied field
+ * derivatives; then f_tilde = f - dt/2 Omega(f).  d is 9 arrays [ny][nx]:
+ * rho_t, ux_t, uy_t, rho_x, ux_x, uy_x, rho_y, ux_y, uy_y. */
+int orc_init_chapman_enskog(const orc_problem *p, const double *rho,
+                            const double *ux, const double *uy,
+                            const double *const *d, double *f_tilde);
+
+/* The explicit time step (DUGKS or BKG in finite-volume form), nsteps times,
+ * in place on f_tilde [9][ny][nx]. */
+int orc_step(const orc_problem *p, double *f_tilde, long long nsteps);
+/* BKG in its finite-difference Lax-Wendroff form (Eqs. bkgfd and
+ * central_schemes); uniform periodic meshes only. */
+int orc_step_bkg_fd(const orc_problem *p, double *f_tilde, long long nsteps);
+/* Brute force from the implicit (trapezoidal) forms, Eqs. eq_raw and
+ * eq_charraw (DUGKS) or splic_c then bkgfd (BKG), on the ORIGINAL
+ * distribution f [9][ny][nx]; periodic meshes only.  The implicit relations
+ * are solved by fixed-point iteration until the residual is at rounding
+ * level (8 eps (1 + k/tau) max|rhs|). */
+int orc_step_implicit(const orc_problem *p, double *f, long long nsteps);
+
+/* f_tilde = f - dt/2 Omega(f) (transform of Sec 2.2), element-wise. */
+int orc_tilde_from_f(const orc_problem *p, const double *f, double *f_tilde);
+
+/* Diagnostics. */
+int orc_moments(const orc_problem *p, const double *f_tilde, double *rho,
+                double *ux, double *uy);
+/* out[0] = sum rho |V|, out[1..2] = sum rho u |V|. */
+int orc_conserved(const orc_problem *p, const double *f_tilde, double *out);
+/* Sec 3.1: E_u = sqrt(sum |u_n - u_a|^2) / sqrt(sum |u_a|^2) over cells. */
+int orc_l2_error_u(const orc_problem *p, const double *f_tilde,
+                   const double *ua, const double *va, double *eu);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,430 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test ties one part of the oracle to something other than itself:
+closed forms, invariants, a brute-force solve of the implicit forms, the
+paper's printed Table 1, textbook constants.  The mutation tests at the end
+plant plausible mistakes in a copy of the oracle and check a pin catches each.
+"""
+import math
+import os
+import pathlib
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+RT = W.RT_LATTICE
+GOLDEN = pathlib.Path(__file__).parent / "golden"
+
+
+def _per():
+    return [("periodic", -W.INF, W.INF, 0.0, 0.0, 0.0)]
+
+
+def periodic_case(nx, ny, scheme="dugks", tau=0.05, dt=None, xf=None, yf=None, Lx=1.0, Ly=1.0):
+    xf = W.uniform_faces(nx, 0.0, Lx) if xf is None else xf
+    yf = W.uniform_faces(ny, 0.0, Ly) if yf is None else yf
+    if dt is None:
+        dt = W.cfl_dt(xf, yf, 0.5)
+    return dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT, tau=tau, dt=dt, scheme=scheme,
+                bc=[_per(), _per(), _per(), _per()])
+
+
+# ---------------------------------------------------------------- Sec 2.1
+
+def test_velocity_set_matches_angle_definition():
+    """Sec 2.1: xi from the printed cos/sin definition, weights, reverses."""
+    for rt in (RT, 0.5, 2.0):
+        xi, w, opp = O.d2q9(rt)
+        c = math.sqrt(3 * rt)
+        ref = [(0.0, 0.0)]
+        for a in range(1, 5):
+            th = (a - 1) * math.pi / 2
+            ref.append((c * math.cos(th), c * math.sin(th)))
+        for a in range(5, 9):
+            th = (2 * a - 9) * math.pi / 4
+            ref.append((math.sqrt(2) * c * math.cos(th), math.sqrt(2) * c * math.sin(th)))
+        np.testing.assert_allclose(xi, np.array(ref), atol=1e-14 * c, rtol=0)
+        np.testing.assert_array_equal(w, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        np.testing.assert_array_equal(xi[opp], -xi)
+        # lattice isotropy: sum w = 1, sum w xi = 0, sum w xi xi = c_s^2 I
+        assert abs(w.sum() - 1) < 1e-15
+        np.testing.assert_allclose(w @ xi, 0, atol=1e-15)
+        np.testing.assert_allclose((w[:, None, None] * xi[:, :, None] * xi[:, None, :]).sum(0),
+                                   rt * np.eye(2), atol=1e-15)
+
+
+def test_equilibrium_moments_closed_form():
+    """Eq. equilibrium reproduces rho, rho u and rho c_s^2 I + rho u u exactly."""
+    rng = np.random.default_rng(0)
+    xi, _, _ = O.d2q9(RT)
+    for _ in range(50):
+        rho, ux, uy = 1 + 0.3 * rng.uniform(-1, 1), 0.2 * rng.uniform(-1, 1), 0.2 * rng.uniform(-1, 1)
+        f = O.equilibrium(RT, rho, ux, uy)
+        u = np.array([ux, uy])
+        assert abs(f.sum() - rho) < 1e-15
+        np.testing.assert_allclose(f @ xi, rho * u, atol=1e-15)
+        pi2 = (f[:, None, None] * xi[:, :, None] * xi[:, None, :]).sum(0)
+        np.testing.assert_allclose(pi2, rho * RT * np.eye(2) + rho * np.outer(u, u), atol=2e-15)
+
+
+def test_dt_from_cfl_and_faces():
+    """Eq. eq:cfl: max |xi| dt / dx_min equals the CFL number; face helpers."""
+    xf = O.faces_tanh(40, 0.0, 1.0, 1.5)
+    yf = O.faces_geometric(30, 0.0, 1e-3, 1.05)
+    dt = O.dt_from_cfl(xf, yf, RT, 0.5)
+    dmin = min(np.diff(xf).min(), np.diff(yf).min())
+    assert abs(dt * math.sqrt(2) * math.sqrt(3 * RT) / dmin - 0.5) < 1e-15
+    np.testing.assert_allclose(O.faces_uniform(8, -1.0, 1.0), np.linspace(-1, 1, 9), atol=1e-15)
+    np.testing.assert_allclose(xf[[0, -1]], [0.0, 1.0], atol=1e-15)
+    np.testing.assert_allclose(xf + xf[::-1], 1.0, atol=1e-15)  # symmetric clustering
+    d = np.diff(yf)
+    np.testing.assert_allclose(d[1:] / d[:-1], 1.05, rtol=1e-12)
+    np.testing.assert_allclose(xf, W.tanh_faces(40, 0.0, 1.0, 1.5), atol=1e-15)
+    np.testing.assert_allclose(yf, W.geometric_faces(30, 0.0, 1e-3, 1.05), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("stretched", [False, True])
+def test_uniform_flow_is_a_fixed_point(scheme, stretched):
+    """A uniform equilibrium stays put: transform coefficients sum to one and
+    the linear reconstruction is exact for constants (periodic mesh)."""
+    xf = W.tanh_faces(12, 0.0, 1.0, 1.2) if stretched else None
+    case = periodic_case(12, 10, scheme, tau=0.02, xf=xf)
+    f0 = O.init_equilibrium(case, np.full((10, 12), 1.01), np.full((10, 12), 0.03),
+                            np.full((10, 12), -0.02))
+    f = O.step(case, f0, 20)
+    assert np.max(np.abs(f - f0)) < 2e-16 * 20
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_conservation_periodic(scheme):
+    """Eq. eq:convervation + flux telescoping: mass and momentum are exact on a
+    periodic mesh, stretched in x."""
+    case = periodic_case(16, 12, scheme, tau=0.01, xf=W.tanh_faces(16, 0.0, 1.0, 1.0))
+    (r, u, v), delta = W.random_state(case, 3, amp_neq=1e-3)
+    f0 = O.init_equilibrium(case, r, u, v) + delta
+    c0 = O.conserved(case, f0)
+    c1 = O.conserved(case, O.step(case, f0, 40))
+    assert abs(c1[0] - c0[0]) < 1e-14 * abs(c0[0])
+    assert np.max(np.abs(c1[1:] - c0[1:])) < 1e-14 * abs(c0[0])
+
+
+@pytest.mark.parametrize("kind", ["wall", "diffuse"])
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_closed_cavity_conserves_mass(kind, scheme):
+    """Sec 2.5: bounce-back gives zero net mass flux through a wall moving
+    tangentially; the diffuse wall is built for zero normal mass flux."""
+    case, (r, u, v) = W.cavity(12, Re=100, scheme=scheme, kind=kind)
+    (r, u, v), _ = W.random_state(case, 4)
+    f0 = O.init_equilibrium(case, r, u, v)
+    m0 = O.conserved(case, f0)[0]
+    m1 = O.conserved(case, O.step(case, f0, 60))[0]
+    assert abs(m1 - m0) < 1e-14 * m0
+
+
+def test_fv_form_equals_fd_form():
+    """Sec 2.3: BKG as a finite-volume scheme with the face values of Eq.
+    f_left equals the Lax-Wendroff finite-difference form (Eqs. bkgfd,
+    central_schemes) on a uniform periodic mesh."""
+    case = periodic_case(14, 10, "bkg", tau=0.004, Lx=1.4)
+    (r, u, v), delta = W.random_state(case, 5, amp_neq=1e-3)
+    f0 = O.init_equilibrium(case, r, u, v) + delta
+    a = O.step(case, f0, 12)
+    b = O.step_bkg_fd(case, f0, 12)
+    assert np.max(np.abs(a - b)) < 2e-15
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("dt_over_tau", [0.5, 10.0])
+def test_explicit_step_matches_implicit_brute_force(scheme, dt_over_tau):
+    """The explicit transforms (f_tilde, f_bar^+, f_tilde^+, back-transform)
+    against a fixed-point solve of the implicit trapezoidal forms: Eqs.
+    eq_raw and eq_charraw (DUGKS), Eq. splic_c then Lax-Wendroff (BKG).
+    8x8 periodic mesh (stretched in y for DUGKS)."""
+    yf = W.tanh_faces(8, 0.0, 1.0, 1.0) if scheme == "dugks" else None
+    case = periodic_case(8, 8, scheme, yf=yf)
+    case["tau"] = case["dt"] / dt_over_tau
+    (r, u, v), delta = W.random_state(case, 6, amp_neq=5e-3)
+    f_orig = O.init_equilibrium(case, r, u, v) + delta
+    e = O.step(case, O.tilde_from_f(case, f_orig), 10)
+    i = O.tilde_from_f(case, O.step_implicit(case, f_orig, 10))
+    assert np.max(np.abs(e - i)) < 1e-14
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_collisionless_limit_is_lax_wendroff(scheme):
+    """tau -> infinity: both schemes reduce to 2-D Lax-Wendroff advection per
+    direction (Sec 2.4's flux analysis).  One Fourier mode per alpha is
+    multiplied each step by G = 1 - i(nx sin tx + ny sin ty) - nx^2(1-cos tx)
+    - ny^2(1-cos ty) - nx ny sin tx sin ty, nu = xi dt / dx, t = k dx."""
+    n, steps = 16, 7
+    case = periodic_case(n, n, scheme, tau=1e30)
+    dx = 1.0 / n
+    xi, w, _ = O.d2q9(RT)
+    x, y = np.meshgrid(W.centres(case["xf"]), W.centres(case["yf"]))
+    kx, ky = 2 * math.pi * 2, 2 * math.pi * 3
+    phase = np.exp(1j * (kx * x + ky * y))
+    f0 = np.array([w[a] * (1.0 + 1e-3 * phase.real) for a in range(9)])
+    f = O.step(case, f0, steps)
+    for a in range(9):
+        nux, nuy = xi[a] * case["dt"] / dx
+        tx, ty = kx * dx, ky * dx
+        G = (1 - 1j * (nux * math.sin(tx) + nuy * math.sin(ty)) - nux ** 2 * (1 - math.cos(tx))
+             - nuy ** 2 * (1 - math.cos(ty)) - nux * nuy * math.sin(tx) * math.sin(ty))
+        ref = w[a] * (1.0 + 1e-3 * (G ** steps * phase).real)
+        assert np.max(np.abs(f[a] - ref)) < 1e-15, a
+
+
+def test_unit_courant_axis_velocity_shifts_exactly():
+    """Special case of the closed form: xi dt / dx = 1 on an axis direction
+    makes G = exp(-i t), an exact one-cell shift of any field."""
+    n = 12
+    case = periodic_case(n, n, "dugks", tau=1e30, dt=1.0 / n / math.sqrt(3 * RT))
+    rng = np.random.default_rng(7)
+    f0 = np.array([O.equilibrium(RT, 1.0, 0, 0)[a] * (1 + 1e-2 * rng.uniform(-1, 1, (n, n)))
+                   for a in range(9)])
+    f = O.step(case, f0, 1)
+    np.testing.assert_allclose(f[1], np.roll(f0[1], 1, axis=1), atol=1e-16, rtol=0)
+    np.testing.assert_allclose(f[2], np.roll(f0[2], 1, axis=0), atol=1e-16, rtol=0)
+    np.testing.assert_allclose(f[3], np.roll(f0[3], -1, axis=1), atol=1e-16, rtol=0)
+    np.testing.assert_allclose(f[4], np.roll(f0[4], -1, axis=0), atol=1e-16, rtol=0)
+
+
+def _smooth_periodic_faces(n, amp):
+    s = np.arange(n + 1) / n
+    return s + amp * np.sin(2 * np.pi * s) / (2 * np.pi)  # widths ~ 1 + amp cos(2 pi s)
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_stretched_mesh_advection_is_second_order(scheme):
+    """The linear reconstruction on a stretched mesh (theta-weighted value,
+    normal and tangential slopes) is second-order accurate: collisionless
+    advection of a smooth wave on a smoothly stretched periodic mesh has an
+    error that falls about 4x per mesh doubling."""
+    errs = []
+    xi, w, _ = O.d2q9(RT)
+    for n in (32, 64):
+        xf, yf = _smooth_periodic_faces(n, 0.3), _smooth_periodic_faces(n, 0.4)
+        case = periodic_case(n, n, scheme, tau=1e30, xf=xf, yf=yf, dt=W.cfl_dt(xf, yf, 0.4))
+        x, y = np.meshgrid(W.centres(xf), W.centres(yf))
+        steps = int(round(0.25 / case["dt"]))
+        T = steps * case["dt"]
+        f0 = np.array([w[a] * (1 + 0.01 * np.sin(2 * np.pi * (x + 2 * y))) for a in range(9)])
+        ex = np.array([w[a] * (1 + 0.01 * np.sin(2 * np.pi * ((x - xi[a, 0] * T) + 2 * (y - xi[a, 1] * T))))
+                       for a in range(9)])
+        errs.append(np.sqrt(np.mean((O.step(case, f0, steps) - ex) ** 2)))
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_linear_fields_advect_exactly_on_random_mesh(scheme):
+    """Linear reconstruction is exact for linear fields on any tensor mesh:
+    with collisions off, one step of a linear f moves every cell average by
+    exactly -dt xi . grad f (cells two or more away from the periodic seam)."""
+    rng = np.random.default_rng(9)
+    n = 12
+    xf = np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n))]) / n
+    yf = np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n))]) / n
+    case = periodic_case(n, n, scheme, tau=1e30, xf=xf, yf=yf, dt=W.cfl_dt(xf, yf, 0.4))
+    xi, w, _ = O.d2q9(RT)
+    x, y = np.meshgrid(W.centres(xf), W.centres(yf))
+    gx, gy = 0.7e-2, 1.3e-2
+    f0 = np.array([w[a] * (1 + gx * x + gy * y) for a in range(9)])
+    f1 = O.step(case, f0, 1)
+    dt = case["dt"]
+    ex = np.array([w[a] * (1 + gx * (x - xi[a, 0] * dt) + gy * (y - xi[a, 1] * dt)) for a in range(9)])
+    inner = (slice(None), slice(2, n - 2), slice(2, n - 2))
+    assert np.max(np.abs(f1[inner] - ex[inner])) < 1e-16
+
+
+# ---------------------------------------------------------------- walls / BCs
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_couette_flow_is_linear(scheme):
+    """Sec 2.5 walls (ghost extrapolation + bounce-back with U_w): plane
+    Couette flow reaches the exact linear profile u = U y / H."""
+    case, (r, u, v) = W.couette(4, 16, U=0.05, nu=0.1, scheme=scheme)
+    n = int(3.0 / case["nu"] / case["dt"])
+    f = O.step(case, O.init_equilibrium(case, r, u, v), n)
+    _, uu, vv = O.moments(case, f)
+    ua = case["U"] * W.centres(case["yf"])
+    assert np.max(np.abs(uu - ua[:, None])) < 1e-7 * case["U"]
+    assert np.max(np.abs(vv)) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_symmetry_plane_equals_mirrored_full_domain(scheme):
+    """Symmetry ghosts: the half domain with a symmetry plane reproduces the
+    upper half of the mirrored full domain."""
+    nx, nyh = 8, 8
+    xf = W.uniform_faces(nx, 0, 1.0)
+    base = dict(nx=nx, RT=RT, tau=0.01, dt=0.02, scheme=scheme)
+    lid = W.wall(0.03, 0.0)
+    full = dict(base, ny=2 * nyh, xf=xf, yf=W.uniform_faces(2 * nyh, -1.0, 1.0),
+                bc=[_per(), _per(), [lid], [lid]])
+    half = dict(base, ny=nyh, xf=xf, yf=W.uniform_faces(nyh, 0, 1.0),
+                bc=[_per(), _per(), [("symmetry", -W.INF, W.INF, 1, 0, 0)], [lid]])
+    (rh, uh, vh), _ = W.random_state(half, 8)
+    rf, uf, vf = (np.concatenate([rh[::-1], rh]), np.concatenate([uh[::-1], uh]),
+                  np.concatenate([-vh[::-1], vh]))
+    ff = O.step(full, O.init_equilibrium(full, rf, uf, vf), 30)
+    fh = O.step(half, O.init_equilibrium(half, rh, uh, vh), 30)
+    assert np.max(np.abs(ff[:, nyh:, :] - fh)) < 1e-15
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_free_stream_boundaries_keep_uniform_flow(scheme):
+    """Inflow equilibrium (W, N), zero-gradient outflow (E) and a symmetry
+    plane (S) on a stretched mesh keep the free stream exactly."""
+    case, (r, u, v) = W.flat_plate(nx_up=8, nx_plate=16, ny=12, scheme=scheme)
+    case["bc"][2] = [("symmetry", -W.INF, W.INF, 1.0, 0.0, 0.0)]
+    f0 = O.init_equilibrium(case, r, u, v)
+    assert np.max(np.abs(O.step(case, f0, 50) - f0)) < 1e-16
+
+
+# ---------------------------------------------------------------- physics
+
+def test_taylor_green_decay_and_viscosity():
+    """Sec 3.1 / Eq. nu_tau: the TG velocity amplitude decays as
+    exp(-2 nu t) with nu = tau RT.  The rate is fitted between t = 2 and
+    t = 6 (after the start-up layer of a few tau that f = f_eq leaves) and
+    matches tau RT to 1% on 32^2 and 64^2 meshes at CFL 0.5.  (At fixed CFL
+    dt shrinks with dx, so this error mixes the O(dx^2) and O(dt) parts;
+    second-order spatial accuracy is pinned by Table 1 instead.)"""
+    errs = []
+    for n in (32, 64):
+        case, (r, u, v) = W.taylor_green_box(n)
+        ua0, va0 = W.taylor_green_box_analytic(case, 0.0)
+        f = O.init_equilibrium(case, r, u, v)
+        amps, times, done = [], [], 0
+        for t in (2.0, 6.0):
+            steps = int(round(t / case["dt"]))
+            f = O.step(case, f, steps - done)
+            done = steps
+            _, uu, vv = O.moments(case, f)
+            amps.append((np.sum(uu * ua0) + np.sum(vv * va0)) / (np.sum(ua0 ** 2) + np.sum(va0 ** 2)))
+            times.append(steps * case["dt"])
+        nu_fit = math.log(amps[0] / amps[1]) / (2 * (times[1] - times[0]))
+        errs.append(abs(nu_fit / case["nu"] - 1))
+    assert max(errs) < 0.01, errs
+
+
+def _golden_table1():
+    rows = {}
+    for line in (GOLDEN / "table1_tv_nerr.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            s, n, e = line.split()
+            rows[(s, int(n))] = float(e)
+    return rows
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_table1_taylor_green_error_n16(scheme):
+    """Table tab:tv_Nerr (Sec 3.1), N = 16: E_u(t_c) with the paper's set-up
+    (dt = 2 tau, Chapman-Enskog start, round(t_c/dt) steps) matches the
+    printed value to its four digits."""
+    case, (r, u, v), d, tc = W.taylor_green_paper(16, scheme)
+    f = O.init_chapman_enskog(case, r, u, v, d)
+    n = int(round(tc / case["dt"]))
+    f = O.step(case, f, n)
+    ua, va = W.taylor_green_paper_analytic(case, n * case["dt"])
+    eu = O.l2_error_u(case, f, ua, va)
+    ref = _golden_table1()[(scheme, 16)]
+    assert abs(eu / ref - 1) < 5e-4, (eu, ref)
+
+
+def test_blasius_wall_shear():
+    """Blasius solution used for the flat plate (Sec 3.3): f''(0) = 0.33206."""
+    from oracle import blasius
+    eta, f, fp, fpp, fpp0 = blasius.solve()
+    assert abs(fpp0 - 0.332057) < 2e-6
+    assert abs(fp[-1] - 1.0) < 1e-6
+    # displacement thickness integral: int (1 - f') d eta = 1.7208
+    assert abs(np.trapezoid(1 - fp, eta) - 1.7208) < 1e-3
+
+
+# ---------------------------------------------------------------- mutations
+
+MUTATIONS = {
+    # dropped tangential term of the reconstruction
+    "tangential": ("out[a] = value - h * (v->xi[a][0] * slope_n + v->xi[a][1] * slope_t);",
+                   "out[a] = value - h * (v->xi[a][0] * slope_n);"),
+    # wrong sign of the update's flux
+    "flux_sign": ("ft[a * n + k] = TP[a * n + k] - dt / vol * out_flux;",
+                  "ft[a * n + k] = TP[a * n + k] + dt / vol * out_flux;"),
+    # f_bar^+ coefficient with dt in place of h
+    "fbar_coef": ("phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);",
+                  "phi = ((2.0 * tau - dt) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);"),
+    # back-transform at the face uses dt = 2h instead of h
+    "face_back": ("val[a] = (2.0 * tau * val[a] + h * fe[a]) / (2.0 * tau + h);",
+                  "val[a] = (2.0 * tau * val[a] + 2.0 * h * fe[a]) / (2.0 * tau + 2.0 * h);"),
+    # bounce-back with the wrong sign of the wall term
+    "bounce_sign": ("val[v->opp[a]] = orig[a] - 2.0 * v->w[a] * xu / v->cs2;",
+                    "val[v->opp[a]] = orig[a] + 2.0 * v->w[a] * xu / v->cs2;"),
+    # transposed theta in the y-face blend
+    "theta_swap": ("double value = (1.0 - th) * pl + th * pr;\n    double slope_n = (pr - pl) / (yr - yl);",
+                   "double value = th * pl + (1.0 - th) * pr;\n    double slope_n = (pr - pl) / (yr - yl);"),
+}
+
+
+def _mutant(tmp_path, name):
+    src = (pathlib.Path(O.__file__).parent / "dvbe_oracle.c").read_text()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, name
+    d = tmp_path / name
+    d.mkdir()
+    shutil.copy(pathlib.Path(O.__file__).parent / "dvbe_oracle.h", d)
+    (d / "dvbe_oracle.c").write_text(src.replace(old, new))
+    so = d / "lib.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(so), str(d / "dvbe_oracle.c"), "-lm"])
+    return str(so)
+
+
+def _pins_with(so_path):
+    """Run a compact set of the pins above against another build of the
+    oracle; returns the names of the pins that fail."""
+    import ctypes
+    saved = O._lib
+    O._lib = None
+    real_build = O.build
+    O.build = lambda force=False: so_path
+    failed = []
+    try:
+        O.lib()
+        checks = {
+            "fv_fd": lambda: test_fv_form_equals_fd_form(),
+            "implicit": lambda: test_explicit_step_matches_implicit_brute_force("dugks", 10.0),
+            "lw": lambda: test_collisionless_limit_is_lax_wendroff("dugks"),
+            "couette": lambda: test_couette_flow_is_linear("dugks"),
+            "tg": lambda: test_taylor_green_decay_and_viscosity(),
+            "stretched_fp": lambda: test_uniform_flow_is_a_fixed_point("dugks", True),
+            "stretched_order": lambda: test_stretched_mesh_advection_is_second_order("dugks"),
+            "linear_exact": lambda: test_linear_fields_advect_exactly_on_random_mesh("dugks"),
+        }
+        for k, fn in checks.items():
+            try:
+                fn()
+            except (AssertionError, O.OracleError):
+                failed.append(k)
+    finally:
+        O.build = real_build
+        O._lib = saved
+    return failed
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistakes_are_caught(tmp_path, name):
+    failed = _pins_with(_mutant(tmp_path, name))
+    assert failed, f"mutation {name} passed every pin"

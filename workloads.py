@@ -1,0 +1,305 @@
+"""Seeded synthetic workloads shared by the tests, the bench and smoke().
+
+This module only describes problems: face coordinates of the meshes, initial
+macroscopic fields (rho, u), analytic reference fields, random perturbations
+and the batched case table.  It holds none of the scheme's arithmetic (no
+equilibrium, no transforms, no fluxes); the CUDA library and the CPU oracle
+each turn these inputs into distributions on their own.
+
+A case is a plain dict:
+
+    nx, ny          cells
+    xf, yf          face coordinates (float64, nx+1 / ny+1)
+    RT, tau, dt     velocity-model temperature, relaxation time, time step
+    scheme          "dugks" | "bkg"
+    bc              [W, E, S, N]; each a list of (kind, s0, s1, rho, ux, uy)
+                    kind in periodic | wall | diffuse | inflow | outflow | symmetry
+
+Workloads follow the paper's test problems (Sec 3): Taylor-Green vortex,
+lid-driven cavity, flat-plate boundary layer.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+RT_LATTICE = 1.0 / 3.0  # c_s = 1/sqrt(3) in all of the paper's runs (Sec 3)
+INF = 1.0e300           # segment end that covers a whole side
+
+
+def uniform_faces(n: int, a: float, b: float) -> np.ndarray:
+    return a + (b - a) * np.arange(n + 1, dtype=np.float64) / n
+
+
+def tanh_faces(n: int, a: float, b: float, beta: float) -> np.ndarray:
+    """Both-end clustering: x(s) = a + (b-a) (1 + tanh(beta(2s-1))/tanh(beta)) / 2."""
+    s = np.arange(n + 1, dtype=np.float64) / n
+    return a + (b - a) * 0.5 * (1.0 + np.tanh(beta * (2.0 * s - 1.0)) / math.tanh(beta))
+
+
+def geometric_faces(n: int, a: float, d0: float, ratio: float) -> np.ndarray:
+    i = np.arange(n + 1, dtype=np.float64)
+    if ratio == 1.0:
+        return a + d0 * i
+    return a + d0 * (ratio ** i - 1.0) / (ratio - 1.0)
+
+
+def centres(f: np.ndarray) -> np.ndarray:
+    return 0.5 * (f[1:] + f[:-1])
+
+
+def cfl_dt(xf, yf, cfl: float, RT: float = RT_LATTICE) -> float:
+    """Time step for a stated CFL number: cfl * (smallest cell width) / |xi|_max
+    with |xi|_max = sqrt(6 RT) for D2Q9 (problem set-up, Sec 2.2)."""
+    dmin = min(np.min(np.diff(xf)), np.min(np.diff(yf)))
+    return cfl * dmin / math.sqrt(6.0 * RT)
+
+
+def periodic_bc():
+    side = [("periodic", -INF, INF, 0.0, 0.0, 0.0)]
+    return [list(side), list(side), list(side), list(side)]
+
+
+def wall(ux=0.0, uy=0.0, kind="wall", s0=-INF, s1=INF):
+    return (kind, s0, s1, 1.0, ux, uy)
+
+
+# --------------------------------------------------------------------------
+# Taylor-Green vortex
+# --------------------------------------------------------------------------
+
+def taylor_green_box(n: int, u0: float = 0.01, nu: float = 0.05, cfl: float = 0.5,
+                     scheme: str = "dugks", dt_over_tau: float | None = None):
+    """Periodic [0, 2 pi]^2 Taylor-Green vortex, rho0 = 1, f = f_eq initially.
+
+    u = -u0 cos x sin y, v = u0 sin x cos y, p = p0 - rho0 u0^2 (cos 2x + cos 2y)/4,
+    rho = rho0 + (p - p0)/RT.  Velocity decays as exp(-2 nu t).
+    dt = cfl * dx / sqrt(6 RT) (cfl = 0.5 gives dt = 0.5 dx / sqrt(2)).
+    With dt_over_tau given, nu is set from the CFL time step instead.
+    """
+    L = 2.0 * math.pi
+    xf = uniform_faces(n, 0.0, L)
+    yf = uniform_faces(n, 0.0, L)
+    dt = cfl_dt(xf, yf, cfl)
+    if dt_over_tau is not None:
+        tau = dt / dt_over_tau
+        nu = tau * RT_LATTICE
+    tau = nu / RT_LATTICE
+    case = dict(nx=n, ny=n, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme,
+                bc=periodic_bc(), nu=nu, u0=u0, name=f"taylor-green {n}x{n}")
+    x, y = np.meshgrid(centres(xf), centres(yf))
+    rho = 1.0 - u0 * u0 * (np.cos(2 * x) + np.cos(2 * y)) / 4.0 / RT_LATTICE
+    ux = -u0 * np.cos(x) * np.sin(y)
+    uy = u0 * np.sin(x) * np.cos(y)
+    return case, (rho, ux, uy)
+
+
+def taylor_green_box_analytic(case, t: float):
+    x, y = np.meshgrid(centres(case["xf"]), centres(case["yf"]))
+    d = math.exp(-2.0 * case["nu"] * t)
+    u0 = case["u0"]
+    return -u0 * np.cos(x) * np.sin(y) * d, u0 * np.sin(x) * np.cos(y) * d
+
+
+def taylor_green_paper(n: int, scheme: str = "dugks"):
+    """The set-up of Sec 3.1: unit box, U0 = 1e-2/sqrt(3), nu = 1e-4/sqrt(3),
+    dt = 2 tau, Chapman-Enskog initial state from the analytic solution.
+
+    Returns (case, fields, derivs, t_c) with derivs = (rho_t, ux_t, uy_t, rho_x,
+    ux_x, uy_x, rho_y, ux_y, uy_y) of the analytic solution at t = 0 and
+    t_c = ln 2 / (8 nu pi^2) the half-life time.
+    """
+    U0 = 1e-2 / math.sqrt(3.0)
+    nu = 1e-4 / math.sqrt(3.0)
+    tau = nu / RT_LATTICE
+    dt = 2.0 * tau
+    xf = uniform_faces(n, 0.0, 1.0)
+    yf = uniform_faces(n, 0.0, 1.0)
+    case = dict(nx=n, ny=n, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme,
+                bc=periodic_bc(), nu=nu, U0=U0, name=f"taylor-green (paper) {n}x{n}")
+    pi = math.pi
+    x, y = np.meshgrid(centres(xf), centres(yf))
+    c2x, s2x, c2y, s2y = np.cos(2 * pi * x), np.sin(2 * pi * x), np.cos(2 * pi * y), np.sin(2 * pi * y)
+    ux = -U0 * c2x * s2y
+    uy = U0 * s2x * c2y
+    p = -U0 * U0 / 4.0 * (np.cos(4 * pi * x) + np.cos(4 * pi * y))
+    rho = 1.0 + p / RT_LATTICE
+    derivs = (
+        -16.0 * pi * pi * nu * p / RT_LATTICE,          # rho_t
+        -8.0 * pi * pi * nu * ux,                       # ux_t
+        -8.0 * pi * pi * nu * uy,                       # uy_t
+        pi * U0 * U0 * np.sin(4 * pi * x) / RT_LATTICE,  # rho_x
+        2.0 * pi * U0 * s2x * s2y,                      # ux_x
+        2.0 * pi * U0 * c2x * c2y,                      # uy_x
+        pi * U0 * U0 * np.sin(4 * pi * y) / RT_LATTICE,  # rho_y
+        -2.0 * pi * U0 * c2x * c2y,                     # ux_y
+        -2.0 * pi * U0 * s2x * s2y,                     # uy_y
+    )
+    t_c = math.log(2.0) / (8.0 * nu * pi * pi)
+    return case, (rho, ux, uy), derivs, t_c
+
+
+def taylor_green_paper_analytic(case, t: float):
+    pi = math.pi
+    x, y = np.meshgrid(centres(case["xf"]), centres(case["yf"]))
+    d = math.exp(-8.0 * pi * pi * case["nu"] * t)
+    U0 = case["U0"]
+    return (-U0 * np.cos(2 * pi * x) * np.sin(2 * pi * y) * d,
+            U0 * np.sin(2 * pi * x) * np.cos(2 * pi * y) * d)
+
+
+# --------------------------------------------------------------------------
+# Lid-driven cavity, Couette flow, flat plate
+# --------------------------------------------------------------------------
+
+def cavity(n: int, Re: float = 1000.0, U: float = 0.1, cfl: float = 0.5, scheme: str = "dugks",
+           stretch_beta: float | None = None, kind: str = "wall"):
+    """Unit square, lid (north wall) moving at U in x, other walls at rest, fluid
+    at rest initially; nu = U L / Re.  Optional tanh clustering toward all walls."""
+    if stretch_beta:
+        xf = tanh_faces(n, 0.0, 1.0, stretch_beta)
+    else:
+        xf = uniform_faces(n, 0.0, 1.0)
+    yf = xf.copy()
+    nu = U / Re
+    tau = nu / RT_LATTICE
+    dt = cfl_dt(xf, yf, cfl)
+    bc = [[wall(kind=kind)], [wall(kind=kind)], [wall(kind=kind)], [wall(U, 0.0, kind=kind)]]
+    case = dict(nx=n, ny=n, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=bc,
+                nu=nu, name=f"cavity Re={Re:g} {n}x{n}" + (" tanh" if stretch_beta else ""))
+    rho = np.ones((n, n))
+    return case, (rho, np.zeros((n, n)), np.zeros((n, n)))
+
+
+def couette(nx: int, ny: int, U: float = 0.05, nu: float = 0.1, cfl: float = 0.5,
+            scheme: str = "dugks", H: float = 1.0):
+    """Periodic in x; fixed wall at y=0, wall moving at U at y=H; fluid at rest."""
+    xf = uniform_faces(nx, 0.0, H * nx / ny)
+    yf = uniform_faces(ny, 0.0, H)
+    tau = nu / RT_LATTICE
+    dt = cfl_dt(xf, yf, cfl)
+    per = [("periodic", -INF, INF, 0.0, 0.0, 0.0)]
+    bc = [list(per), list(per), [wall()], [wall(U, 0.0)]]
+    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=bc,
+                nu=nu, U=U, name=f"couette {nx}x{ny}")
+    return case, (np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+
+
+def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1,
+               Re_L: float = 1e5, L: float = 1.0, dy_min: float | None = None,
+               height: float = 0.5, up_len: float = 0.5, dx_min: float | None = None,
+               cfl: float = 0.5, scheme: str = "dugks"):
+    """Laminar boundary layer over a flat plate on 0 <= x <= L (Sec 3.3).
+
+    Domain [-up_len, L] x [0, height].  y faces grow geometrically from dy_min
+    with the ratio solved so that ny cells span exactly `height`; x faces are
+    clustered at the leading edge by two geometric runs (upstream and along the
+    plate), each ratio solved to fit its length.  Boundaries: inflow
+    equilibrium (west, north), zero-gradient outflow (east), symmetry before
+    the plate and a no-slip wall on it (south).  Fluid starts at the free stream.
+    """
+    nu = U * L / Re_L
+    if dy_min is None:
+        dy_min = L / 5000.0
+    if dx_min is None:
+        dx_min = L / 2000.0
+    ry = solve_geometric_ratio(ny, dy_min, height)
+    yf = geometric_faces(ny, 0.0, dy_min, ry)
+    yf[-1] = height
+    rp = solve_geometric_ratio(nx_plate, dx_min, L)
+    ru = solve_geometric_ratio(nx_up, dx_min, up_len)
+    plate = geometric_faces(nx_plate, 0.0, dx_min, rp)
+    plate[-1] = L
+    up = -geometric_faces(nx_up, 0.0, dx_min, ru)[::-1]
+    up[0] = -up_len
+    xf = np.concatenate([up[:-1], plate])
+    nx = len(xf) - 1
+    tau = nu / RT_LATTICE
+    dt = cfl_dt(xf, yf, cfl)
+    inflow = ("inflow", -INF, INF, 1.0, U, 0.0)
+    bc = [[inflow], [("outflow", -INF, INF, 1.0, 0.0, 0.0)],
+          [("symmetry", -INF, 0.0, 1.0, 0.0, 0.0), ("wall", 0.0, INF, 1.0, 0.0, 0.0)],
+          [inflow]]
+    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=bc,
+                nu=nu, U=U, ry=ry, name=f"flat plate {nx}x{ny}")
+    return case, (np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx)))
+
+
+def solve_geometric_ratio(n: int, d0: float, length: float) -> float:
+    """Ratio r with d0 (r^n - 1)/(r - 1) = length (bisection)."""
+    if abs(d0 * n - length) <= 1e-15 * length:
+        return 1.0
+    lo, hi = (1.0 + 1e-15, 10.0) if d0 * n < length else (1e-6, 1.0 - 1e-15)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        val = d0 * (mid ** n - 1.0) / (mid - 1.0)
+        if (val < length) == (d0 * n < length):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+# --------------------------------------------------------------------------
+# Random perturbations and batched case tables
+# --------------------------------------------------------------------------
+
+def random_state(case, seed: int, amp_u: float = 0.02, amp_rho: float = 0.01,
+                 amp_neq: float = 0.0):
+    """Smooth-free random macroscopic fields and an optional random
+    non-equilibrium offset delta[9, ny, nx] (scaled per direction by amp_neq)."""
+    rng = np.random.default_rng(seed)
+    ny, nx = case["ny"], case["nx"]
+    rho = 1.0 + amp_rho * rng.uniform(-1, 1, (ny, nx))
+    ux = amp_u * rng.uniform(-1, 1, (ny, nx))
+    uy = amp_u * rng.uniform(-1, 1, (ny, nx))
+    delta = amp_neq * rng.uniform(-1, 1, (9, ny, nx))
+    return (rho, ux, uy), delta
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea, Flood 2014): state += 0x9E3779B97F4A7C15, then
+    the two xor-shift-multiply rounds and a final xor-shift."""
+
+    M = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.s = seed & self.M
+
+    def next_u64(self) -> int:
+        self.s = (self.s + 0x9E3779B97F4A7C15) & self.M
+        z = self.s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.M
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+
+def batched_cases(ncases: int = 512, seed: int = 1511, side_max: int = 512,
+                  side_step: int = 32):
+    """The batched workload: half Taylor-Green boxes, half cavities; schemes
+    alternate DUGKS / BKG; side uniform over multiples of side_step in
+    [side_step, side_max]; Re log-uniform in [100, 5000]; CFL uniform in
+    [0.1, 0.95].  Returns a list of (case, fields)."""
+    g = SplitMix64(seed)
+    out = []
+    nsides = side_max // side_step
+    for i in range(ncases):
+        side = side_step * (1 + min(int(g.uniform() * nsides), nsides - 1))
+        Re = 10.0 ** (2.0 + g.uniform() * (math.log10(5000.0) - 2.0))
+        cfl = 0.1 + 0.85 * g.uniform()
+        scheme = "dugks" if i % 2 == 0 else "bkg"
+        if i < ncases // 2:
+            u0 = 0.01
+            # Re = u0 * 2 pi / nu for the 2 pi periodic box
+            nu = u0 * 2.0 * math.pi / Re
+            case, fields = taylor_green_box(side, u0=u0, nu=nu, cfl=cfl, scheme=scheme)
+        else:
+            case, fields = cavity(side, Re=Re, cfl=cfl, scheme=scheme)
+        case["Re"] = Re
+        case["cfl"] = cfl
+        out.append((case, fields))
+    return out
