@@ -1,0 +1,283 @@
+#!/usr/bin/env python
+"""Throughput of the fused D2Q9 finite-volume step (MLUPS and HBM roofline).
+
+Headline workload: Taylor-Green vortex on a periodic 4096 x 4096 mesh
+(u0 = 0.01, CFL 0.5, dt/tau = 10), DUGKS, FP32 storage and arithmetic.  One
+step = one time step of the whole mesh (all 9 directions of every cell).
+The two f_tilde buffers (604 MB each) are far larger than the 129 MB L2, so
+no flush is needed between steps.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(the plain program the CUDA path is checked against) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+BYTES_PER_CELL = {"f64": 144, "f32": 72, "f32_dev": 72, "f16_dev": 36, "bf16_dev": 36}
+DTYPE = {"f64": "f64", "f32": "f32", "f32_dev": "f32", "f16_dev": "f32 (f16 storage)",
+         "bf16_dev": "f32 (bf16 storage)"}
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=600)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=4096, help="mesh side")
+    p.add_argument("--scheme", default="dugks", choices=["dugks", "bkg"])
+    p.add_argument("--precision", default="f32", choices=list(BYTES_PER_CELL))
+    p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    p.add_argument("--no-autotune", action="store_true")
+    return p.parse_args()
+
+
+def workload(n, scheme):
+    case, fields = W.taylor_green_box(n, u0=0.01, cfl=0.5, scheme=scheme, dt_over_tau=10.0)
+    return case, fields
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(dv, s, stream, torch, K):
+    """K steps on the solver's stream bracketed by CUDA events on that stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    e0.record(stream)
+    s.step_async(K)
+    e1.record(stream)
+    e1.synchronize()
+    s.sync()
+    return e0.elapsed_time(e1) / 1e3, s.launch_count() - l0
+
+
+def cpu_baseline(scheme, budget_s=12.0):
+    """The FP64 oracle as it stands, one host thread, on a 512 x 512 sample of
+    the same Taylor-Green workload, stepped until ~budget_s seconds are spent."""
+    import oracle as O
+    n = 512
+    case, fields = workload(n, scheme)
+    f = O.init_equilibrium(case, *fields)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        f = O.step(case, f, 1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{scheme.upper()} Taylor-Green {n}x{n}, {steps} steps, FP64 C oracle, 1 thread"}
+
+
+def run_reference(a):
+    """Reference arm: the FP64 CPU oracle, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    n = 256
+    case, fields = workload(n, a.scheme)
+    f = O.init_equilibrium(case, *fields)
+    for _ in range(a.warmup):
+        f = O.step(case, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        f = O.step(case, f, 1)
+    dt = time.perf_counter() - t0
+    v = n * n * a.steps / dt / 1e6
+    line = {"metric": "MLUPS", "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"taylor-green {a.n}x{a.n} periodic, {a.scheme.upper()} "
+                                   f"(oracle on a {n}x{n} sample per step)",
+                       "scheme": a.scheme, "precision": "f64"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{a.scheme.upper()} Taylor-Green {n}x{n} per step, 1 thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1511_00242_gb300 as dv
+    from paper_1511_00242_gb300 import build
+    build.build()
+
+    stream = torch.cuda.Stream()
+    case, fields = workload(a.n, a.scheme)
+    cells = a.n * a.n
+    s = dv.Solver(case, precision=a.precision, stream=stream.cuda_stream)
+    s.init_equilibrium(*fields)
+    tuned_ms = None
+    if not a.no_autotune:
+        tuned_ms = s.autotune(3)
+    launch = s.get_launch()
+    s.step(a.warmup)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    t, launches = time_steps(dv, s, stream, torch, a.steps)
+    barrier()
+    ck = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * cells * a.steps / t / 1e6
+    per_launch = t / a.steps
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL[a.precision] * cells / per_launch / 1e9
+
+    # end to end through the C ABI with host buffers: pinned f_tilde in, K
+    # steps, moments out
+    f0 = s.get_f()
+    pin = torch.empty(f0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    pin[...] = f0
+    outs = [torch.empty((a.n, a.n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    barrier()
+    t0 = time.perf_counter()
+    s.init_f(pin)
+    s.step(a.steps)
+    r, u, v = s.moments()
+    barrier()
+    te = time.perf_counter() - t0
+    outs[0][...] = r
+    e2e = {"value": world * cells * a.steps / te / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": pin.nbytes / a.steps, "d2h_bytes_per_step": 3 * cells * 8 / a.steps,
+           "note": "init_f from pinned host f_tilde (float64), the steps, get_moments to host"}
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        # BKG and the other storage modes on the same workload, shorter runs
+        for scheme, prec in (("bkg", "f32"), ("dugks", "f16_dev"), ("bkg", "f16_dev"),
+                             ("dugks", "bf16_dev"), ("dugks", "f32_dev"), ("dugks", "f64")):
+            if scheme == a.scheme and prec == a.precision:
+                continue
+            c2, fl2 = workload(a.n, scheme)
+            s2 = dv.Solver(c2, precision=prec, stream=stream.cuda_stream)
+            s2.init_equilibrium(*fl2)
+            if not a.no_autotune:
+                s2.autotune(2)
+            s2.step(3)
+            k2 = 60 if prec != "f64" else 20
+            t2, _ = time_steps(dv, s2, stream, torch, k2)
+            pl = t2 / k2
+            ach = BYTES_PER_CELL[prec] * cells / pl / 1e9
+            extras[f"{scheme}_{prec}"] = {"MLUPS": cells * k2 / t2 / 1e6, "hbm_GBs": ach,
+                                          "hbm_frac": ach / peak, "launch": s2.get_launch()}
+            s2.close()
+            del s2
+    s.close()
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision], "data": "synthetic",
+            "config": {"workload": f"taylor-green {a.n}x{a.n} periodic, u0=0.01, CFL 0.5, "
+                                   f"dt/tau=10, {a.scheme.upper()}, {a.precision} storage",
+                       "scheme": a.scheme, "precision": a.precision, "cells": cells,
+                       "l2": "inputs larger than L2 (two 604 MB f_tilde buffers), no flush",
+                       "parallelism": f"replicas x{world}", "launch": launch,
+                       "autotune_ms_per_step": tuned_ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "bytes_per_cell": BYTES_PER_CELL[a.precision],
+                         "kernel": f"k_step<{a.scheme}, {a.precision}>"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": ck,
+            "extras": extras,
+        }
+        if not a.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(a.scheme)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -25,6 +25,12 @@
 
 #include <stddef.h>
 
+#if defined(__GNUC__)
+#define DVBE_API __attribute__((visibility("default")))
+#else
+#define DVBE_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -94,31 +100,32 @@ typedef struct {
                        Eqs. bkgfd / central_schemes (identical up to rounding)   */
   double dev_scale; /* s_alpha = dev_scale w_alpha rho0 for *_DEV (0 -> default:
                        1/256 for F16, 1 otherwise)                               */
-  void *cuda_stream; /* cudaStream_t to run on (NULL: the legacy default)        */
+  void *cuda_stream; /* cudaStream_t to run on (NULL: the library creates its own
+                        non-blocking stream)                                    */
 } dvbe_params;
 
 /* ---- velocity set and mesh --------------------------------------------- */
 
 /* Sec 2.1: xi[9][2] (row-major), w[9], opp[9] (xi_opp = -xi). */
-dvbe_status dvbe_d2q9(double RT, double *xi, double *w, int *opp);
+DVBE_API dvbe_status dvbe_d2q9(double RT, double *xi, double *w, int *opp);
 
 /* Face coordinates of a structured tensor mesh (Sec 2.2: cells V_k with faces
  * at x = xf[i], y = yf[j]).  xf has nx+1, yf ny+1 strictly increasing
  * entries; both are copied.  nx, ny >= 2. */
-dvbe_status dvbe_mesh_create(int nx, int ny, const double *xf, const double *yf,
+DVBE_API dvbe_status dvbe_mesh_create(int nx, int ny, const double *xf, const double *yf,
                              dvbe_mesh *out);
-void dvbe_mesh_destroy(dvbe_mesh mesh);
+DVBE_API void dvbe_mesh_destroy(dvbe_mesh mesh);
 /* Cell centres xc[nx], yc[ny] and volumes |V_k| vol[ny][nx] (any may be NULL). */
-dvbe_status dvbe_mesh_geometry(dvbe_mesh mesh, double *xc, double *yc, double *vol);
+DVBE_API dvbe_status dvbe_mesh_geometry(dvbe_mesh mesh, double *xc, double *yc, double *vol);
 /* n+1 faces: uniform on [a, b]; tanh-clustered toward both ends,
  * a + (b-a)(1 + tanh(beta(2s-1))/tanh(beta))/2 with s = i/n; geometric from a
  * with first width d0 and growth ratio. */
-dvbe_status dvbe_faces_uniform(int n, double a, double b, double *out);
-dvbe_status dvbe_faces_tanh(int n, double a, double b, double beta, double *out);
-dvbe_status dvbe_faces_geometric(int n, double a, double d0, double ratio, double *out);
+DVBE_API dvbe_status dvbe_faces_uniform(int n, double a, double b, double *out);
+DVBE_API dvbe_status dvbe_faces_tanh(int n, double a, double b, double beta, double *out);
+DVBE_API dvbe_status dvbe_faces_geometric(int n, double a, double d0, double ratio, double *out);
 /* Eq. eq:cfl: dt = cfl * dx_min / (sqrt(6) c_s), dx_min the smallest cell
  * width of the mesh in either direction. */
-dvbe_status dvbe_dt_from_cfl(dvbe_mesh mesh, double RT, double cfl, double *dt);
+DVBE_API dvbe_status dvbe_dt_from_cfl(dvbe_mesh mesh, double RT, double cfl, double *dt);
 
 /* ---- device memory ------------------------------------------------------ */
 
@@ -128,7 +135,7 @@ dvbe_status dvbe_dt_from_cfl(dvbe_mesh mesh, double RT, double cfl, double *dt);
  * Process-wide; call it while no solver or batch exists. */
 typedef void *(*dvbe_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*dvbe_free_fn)(void *ptr, void *stream, void *ctx);
-dvbe_status dvbe_set_allocator(dvbe_alloc_fn alloc, dvbe_free_fn free_, void *ctx);
+DVBE_API dvbe_status dvbe_set_allocator(dvbe_alloc_fn alloc, dvbe_free_fn free_, void *ctx);
 
 /* ---- one solver ----------------------------------------------------------- */
 
@@ -136,43 +143,43 @@ dvbe_status dvbe_set_allocator(dvbe_alloc_fn alloc, dvbe_free_fn free_, void *ct
  * dx_min is >= 1 without allow_cfl_ge_1), copies the mesh and the boundary
  * segments, allocates two device copies of f_tilde and the geometry
  * tables.  The distribution starts at rest equilibrium (f_tilde = w rho0). */
-dvbe_status dvbe_solver_create(const dvbe_params *params, dvbe_solver *out);
-void dvbe_solver_destroy(dvbe_solver s);
+DVBE_API dvbe_status dvbe_solver_create(const dvbe_params *params, dvbe_solver *out);
+DVBE_API void dvbe_solver_destroy(dvbe_solver s);
 
 /* f_tilde = f_eq(rho, u) (Eq. equilibrium); fields [ny][nx]. */
-dvbe_status dvbe_init_equilibrium(dvbe_solver s, const double *rho, const double *ux,
+DVBE_API dvbe_status dvbe_init_equilibrium(dvbe_solver s, const double *rho, const double *ux,
                                   const double *uy);
 /* Sec 3.1: f = f_eq - tau (d_t f_eq + xi . grad f_eq) with the derivatives of
  * f_eq taken through (rho, u) from d[9] = (rho_t, ux_t, uy_t, rho_x, ux_x,
  * uy_x, rho_y, ux_y, uy_y), then f_tilde = f - dt/2 Omega(f). */
-dvbe_status dvbe_init_chapman_enskog(dvbe_solver s, const double *rho, const double *ux,
+DVBE_API dvbe_status dvbe_init_chapman_enskog(dvbe_solver s, const double *rho, const double *ux,
                                      const double *uy, const double *const *d);
 /* Set / read f_tilde [9][ny][nx]. */
-dvbe_status dvbe_init_f(dvbe_solver s, const double *f_tilde);
-dvbe_status dvbe_get_f(dvbe_solver s, double *f_tilde);
+DVBE_API dvbe_status dvbe_init_f(dvbe_solver s, const double *f_tilde);
+DVBE_API dvbe_status dvbe_get_f(dvbe_solver s, double *f_tilde);
 
 /* Advance nsteps time steps (Eq. eq_update for DUGKS, Eq. lwfv for BKG).
  * Launches are queued on the solver's stream; the call then waits for them
  * and returns DVBE_ERR_DIVERGED if any step met a non-finite or non-positive
  * density (the state is left as it is). */
-dvbe_status dvbe_step(dvbe_solver s, long long nsteps);
+DVBE_API dvbe_status dvbe_step(dvbe_solver s, long long nsteps);
 /* Same launches without the final wait and check. */
-dvbe_status dvbe_step_async(dvbe_solver s, long long nsteps);
+DVBE_API dvbe_status dvbe_step_async(dvbe_solver s, long long nsteps);
 /* Wait for queued work; DVBE_ERR_DIVERGED as for dvbe_step. */
-dvbe_status dvbe_sync(dvbe_solver s);
+DVBE_API dvbe_status dvbe_sync(dvbe_solver s);
 /* Steps taken since creation or the last init. */
-dvbe_status dvbe_step_count(dvbe_solver s, long long *nsteps);
+DVBE_API dvbe_status dvbe_step_count(dvbe_solver s, long long *nsteps);
 
 /* Density and velocity from f_tilde (Eq. macro_var), fields [ny][nx]. */
-dvbe_status dvbe_get_moments(dvbe_solver s, double *rho, double *ux, double *uy);
+DVBE_API dvbe_status dvbe_get_moments(dvbe_solver s, double *rho, double *ux, double *uy);
 /* FP64 sums out[0] = sum rho |V|, out[1] = sum rho u_x |V|, out[2] = sum rho u_y |V|
  * (deterministic order). */
-dvbe_status dvbe_conserved(dvbe_solver s, double out[3]);
+DVBE_API dvbe_status dvbe_conserved(dvbe_solver s, double out[3]);
 /* Relative velocity change since the previous call (FP64, deterministic):
  * r = ||u - u_prev||_2 / ||u||_2 over cells; the first call returns +inf. */
-dvbe_status dvbe_residual(dvbe_solver s, double *r);
+DVBE_API dvbe_status dvbe_residual(dvbe_solver s, double *r);
 /* Sec 3.1: E_u = ||u - u_a||_2 / ||u_a||_2 over cells, FP64. ua, va [ny][nx]. */
-dvbe_status dvbe_l2_error_u(dvbe_solver s, const double *ua, const double *va,
+DVBE_API dvbe_status dvbe_l2_error_u(dvbe_solver s, const double *ua, const double *va,
                             double *eu);
 
 /* Launch shape: cells per warp row are fixed at 30 (32 lanes less two halo
@@ -185,19 +192,19 @@ typedef struct {
   int blocks;
   int graph_chunk;
 } dvbe_launch;
-dvbe_status dvbe_get_launch(dvbe_solver s, dvbe_launch *out);
-dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in);
+DVBE_API dvbe_status dvbe_get_launch(dvbe_solver s, dvbe_launch *out);
+DVBE_API dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in);
 /* Time each candidate launch shape on this solver's own state for `steps`
  * steps and keep the fastest; the state is restored afterwards.  best_ms
  * (may be NULL) receives the fastest time per step. */
-dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms);
+DVBE_API dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms);
 
 /* Device view of the current f_tilde (for timing and inspection): base
  * pointer, row pitch in elements, elements per field, element size. */
-dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch,
+DVBE_API dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch,
                               long long *plane, int *elem_bytes);
 /* Kernel launches issued since creation (every step kernel, init, reduction). */
-dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
+DVBE_API dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
 
 /* ---- batched form --------------------------------------------------------- */
 
@@ -205,27 +212,27 @@ dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
  * persistent launch per scheme over a work queue of all cases' strips.
  * All cases must share one precision.  Each case keeps its own divergence
  * status; a diverged case stops being stepped. */
-dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *out);
-void dvbe_batch_destroy(dvbe_batch b);
-dvbe_status dvbe_batch_init_equilibrium(dvbe_batch b, int icase, const double *rho,
+DVBE_API dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *out);
+DVBE_API void dvbe_batch_destroy(dvbe_batch b);
+DVBE_API dvbe_status dvbe_batch_init_equilibrium(dvbe_batch b, int icase, const double *rho,
                                         const double *ux, const double *uy);
 /* nsteps steps, replayed as CUDA graphs of graph_chunk steps (0: no graph). */
-dvbe_status dvbe_batch_step(dvbe_batch b, long long nsteps, int graph_chunk);
+DVBE_API dvbe_status dvbe_batch_step(dvbe_batch b, long long nsteps, int graph_chunk);
 /* DVBE_OK or DVBE_ERR_DIVERGED for one case (waits for queued work). */
-dvbe_status dvbe_batch_case_status(dvbe_batch b, int icase);
-dvbe_status dvbe_batch_get_moments(dvbe_batch b, int icase, double *rho, double *ux,
+DVBE_API dvbe_status dvbe_batch_case_status(dvbe_batch b, int icase);
+DVBE_API dvbe_status dvbe_batch_get_moments(dvbe_batch b, int icase, double *rho, double *ux,
                                    double *uy);
-dvbe_status dvbe_batch_get_f(dvbe_batch b, int icase, double *f_tilde);
-dvbe_status dvbe_batch_set_launch(dvbe_batch b, const dvbe_launch *in);
-dvbe_status dvbe_batch_autotune(dvbe_batch b, int steps, double *best_ms);
-dvbe_status dvbe_batch_launch_count(dvbe_batch b, long long *count);
+DVBE_API dvbe_status dvbe_batch_get_f(dvbe_batch b, int icase, double *f_tilde);
+DVBE_API dvbe_status dvbe_batch_set_launch(dvbe_batch b, const dvbe_launch *in);
+DVBE_API dvbe_status dvbe_batch_autotune(dvbe_batch b, int steps, double *best_ms);
+DVBE_API dvbe_status dvbe_batch_launch_count(dvbe_batch b, long long *count);
 
 /* ---- misc --------------------------------------------------------------- */
 
 /* Thread-local text of the last failure ("" if none). */
-const char *dvbe_last_error(void);
+DVBE_API const char *dvbe_last_error(void);
 /* Build identification ("libdvbe <arch>"). */
-const char *dvbe_version(void);
+DVBE_API const char *dvbe_version(void);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,64 @@
+// Host-side pieces shared by the single-solver and the batched C ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct dvbe_mesh_ {
+  int nx, ny;
+  std::vector<double> xf, yf;
+};
+
+namespace dvbe {
+
+// A validated problem with its host geometry tables (double precision).
+struct Problem {
+  int nx = 0, ny = 0;
+  std::vector<double> xf, yf;
+  double RT = 0, tau = 0, dt = 0, rho0 = 1, sigma = 1, c = 1, cfl = 0;
+  int user_scheme = 0, kernel = 0, store = 0;
+  bool per_x = false, per_y = false;
+  std::vector<dvbe_bc_segment> bc[4];
+  std::vector<double> xfth, xfs, xct, xcu, yfth, yfs, yct, ycu, volx, voly;
+  double ext[4] = {0, 0, 0, 0};
+  std::vector<unsigned char> segid[4];
+  double a_phi = 0, b_phi = 0, a_tp = 0, b_tp = 0, p_face = 0, q_face = 0, fd_nux = 0, fd_nuy = 0;
+  int pitch = 0, elem = 0;
+  long long plane = 0;
+};
+
+// Device copy of the tables (one allocation).
+struct DeviceProblem {
+  char *blob = nullptr;
+  double *volx = nullptr, *voly = nullptr;
+};
+
+dvbe_status fail(dvbe_status st, const std::string &msg);
+dvbe_status cuda_fail(cudaError_t e, const char *what);
+void *dmalloc(size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+dvbe_status build_problem(const dvbe_params *p, Problem &pb);
+dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cudaStream_t s);
+void set_strips(CaseArgs &a, int H);
+FieldView view_of(const Problem &pb, void *f);
+int sm_count();
+dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStream_t s,
+                         double **out);
+
+cudaError_t launch_step_f64(int scheme, const CaseArgs &a, int blocks, int wpb, cudaStream_t s);
+cudaError_t launch_step_f32(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
+                            cudaStream_t s);
+cudaError_t launch_step_f16(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
+                            cudaStream_t s);
+cudaError_t launch_batch_f64(int scheme, const CaseArgs *c, const long long *p, int n, long long ni,
+                             unsigned long long *q, int blocks, int wpb, cudaStream_t s);
+cudaError_t launch_batch_f32(int store, int scheme, const CaseArgs *c, const long long *p, int n,
+                             long long ni, unsigned long long *q, int blocks, int wpb,
+                             cudaStream_t s);
+cudaError_t launch_batch_f16(int store, int scheme, const CaseArgs *c, const long long *p, int n,
+                             long long ni, unsigned long long *q, int blocks, int wpb,
+                             cudaStream_t s);
+
+} // namespace dvbe

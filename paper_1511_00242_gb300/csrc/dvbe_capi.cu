@@ -1,0 +1,918 @@
+// C ABI of libdvbe (include/dvbe.h): meshes, solvers, device memory, the
+// step driver with optional CUDA-graph replay, readback, reductions and the
+// launch-shape autotuner.  Host code only; the kernels live in
+// step_kernel.cuh (fused step) and aux_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "capi_common.h"
+
+using namespace dvbe;
+
+// ---------------------------------------------------------------------------
+// errors, allocator
+// ---------------------------------------------------------------------------
+
+namespace dvbe {
+
+static thread_local std::string g_err;
+static dvbe_alloc_fn g_alloc = nullptr;
+static dvbe_free_fn g_free = nullptr;
+static void *g_ctx = nullptr;
+
+dvbe_status fail(dvbe_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+dvbe_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(DVBE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dmalloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dfree(void *p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free)
+    g_free(p, (void *)s, g_ctx);
+  else
+    cudaFree(p);
+}
+
+cudaError_t launch_step(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
+                        cudaStream_t s) {
+  switch (store) {
+    case ST_F64:
+      return launch_step_f64(scheme, a, blocks, wpb, s);
+    case ST_F32:
+    case ST_F32_DEV:
+      return launch_step_f32(store, scheme, a, blocks, wpb, s);
+    default:
+      return launch_step_f16(store, scheme, a, blocks, wpb, s);
+  }
+}
+
+cudaError_t launch_step_batch(int store, int scheme, const CaseArgs *c, const long long *p, int n,
+                              long long ni, unsigned long long *q, int blocks, int wpb,
+                              cudaStream_t s) {
+  switch (store) {
+    case ST_F64:
+      return launch_batch_f64(scheme, c, p, n, ni, q, blocks, wpb, s);
+    case ST_F32:
+    case ST_F32_DEV:
+      return launch_batch_f32(store, scheme, c, p, n, ni, q, blocks, wpb, s);
+    default:
+      return launch_batch_f16(store, scheme, c, p, n, ni, q, blocks, wpb, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// problem set-up shared by the solver and the batch
+// ---------------------------------------------------------------------------
+
+static int elem_bytes(int store) {
+  return store == ST_F64 ? 8 : ((store == ST_F16_DEV || store == ST_BF16_DEV) ? 2 : 4);
+}
+
+static bool uniform(const std::vector<double> &f) {
+  const int n = (int)f.size() - 1;
+  const double d0 = f[1] - f[0];
+  for (int i = 1; i < n; ++i)
+    if (std::fabs((f[i + 1] - f[i]) - d0) > 1e-12 * std::fabs(d0)) return false;
+  return true;
+}
+
+static int find_seg(const std::vector<dvbe_bc_segment> &segs, double t) {
+  for (size_t k = 0; k < segs.size(); ++k)
+    if (t >= segs[k].s0 && t < segs[k].s1) return (int)k;
+  return -1;
+}
+
+dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
+  if (!p) return fail(DVBE_ERR_INVALID_ARG, "params is NULL");
+  if (!p->mesh) return fail(DVBE_ERR_INVALID_ARG, "params.mesh is NULL");
+  const dvbe_mesh_ &m = *p->mesh;
+  if (!(p->RT > 0) || !(p->tau > 0) || !(p->dt > 0) || !std::isfinite(p->RT) ||
+      !std::isfinite(p->dt) || std::isnan(p->tau))
+    return fail(DVBE_ERR_INVALID_ARG, "RT, tau and dt must be positive and finite");
+  if (p->scheme != DVBE_DUGKS && p->scheme != DVBE_BKG)
+    return fail(DVBE_ERR_INVALID_ARG, "unknown scheme");
+  if (p->precision < DVBE_F64 || p->precision > DVBE_BF16_DEV)
+    return fail(DVBE_ERR_INVALID_ARG, "unknown precision");
+  pb.nx = m.nx;
+  pb.ny = m.ny;
+  pb.xf = m.xf;
+  pb.yf = m.yf;
+  pb.RT = p->RT;
+  pb.tau = p->tau;
+  pb.dt = p->dt;
+  pb.rho0 = p->rho0 > 0 ? p->rho0 : 1.0;
+  pb.user_scheme = p->scheme;
+  pb.store = p->precision;
+  pb.sigma = p->dev_scale > 0 ? p->dev_scale : (p->precision == DVBE_F16_DEV ? 1.0 / 256.0 : 1.0);
+  bool per[4];
+  for (int s = 0; s < 4; ++s) {
+    if (p->nbc[s] < 1 || p->nbc[s] > DVBE_MAX_SEGMENTS || !p->bc[s])
+      return fail(DVBE_ERR_INVALID_ARG, "each side needs 1.." + std::to_string(DVBE_MAX_SEGMENTS) +
+                                            " boundary segments");
+    pb.bc[s].assign(p->bc[s], p->bc[s] + p->nbc[s]);
+    per[s] = false;
+    for (auto &g : pb.bc[s]) {
+      if (g.kind < DVBE_BC_PERIODIC || g.kind > DVBE_BC_SYMMETRY)
+        return fail(DVBE_ERR_INVALID_ARG, "unknown boundary kind");
+      if (g.kind == DVBE_BC_PERIODIC) per[s] = true;
+      if (g.kind == DVBE_BC_INFLOW_EQ && !(g.rho > 0))
+        return fail(DVBE_ERR_INVALID_ARG, "inflow density must be positive");
+    }
+    if (per[s] && p->nbc[s] != 1)
+      return fail(DVBE_ERR_INVALID_ARG, "a periodic side takes exactly one segment");
+  }
+  if (per[0] != per[1] || per[2] != per[3])
+    return fail(DVBE_ERR_INVALID_ARG, "periodic must pair W with E and S with N");
+  pb.per_x = per[0];
+  pb.per_y = per[2];
+
+  // Eq. eq:cfl
+  double dmin = INFINITY;
+  for (int i = 0; i < pb.nx; ++i) dmin = std::min(dmin, pb.xf[i + 1] - pb.xf[i]);
+  for (int j = 0; j < pb.ny; ++j) dmin = std::min(dmin, pb.yf[j + 1] - pb.yf[j]);
+  pb.cfl = pb.dt * std::sqrt(6.0 * pb.RT) / dmin;
+  if (pb.cfl >= 1.0 && !p->allow_cfl_ge_1) {
+    char b[160];
+    snprintf(b, sizeof b, "CFL number %.6g >= 1 (dt |xi|_max / dx_min); set allow_cfl_ge_1", pb.cfl);
+    return fail(DVBE_ERR_CFL, b);
+  }
+
+  pb.kernel = p->scheme == DVBE_DUGKS ? SC_DUGKS : SC_BKG_FV;
+  if (p->bkg_fd) {
+    if (p->scheme != DVBE_BKG || !pb.per_x || !pb.per_y || !uniform(pb.xf) || !uniform(pb.yf))
+      return fail(DVBE_ERR_UNSUPPORTED,
+                  "the finite-difference BKG form needs BKG on a uniform, doubly periodic mesh");
+    pb.kernel = SC_BKG_FD;
+  }
+
+  // geometry (Sec 2.2 finite volumes on the tensor mesh)
+  const int nx = pb.nx, ny = pb.ny;
+  const double c = std::sqrt(3.0 * pb.RT), h = 0.5 * pb.dt;
+  auto centres = [](const std::vector<double> &f, bool periodic, std::vector<double> &cb) {
+    const int n = (int)f.size() - 1;
+    cb.assign(n + 2, 0.0); // cb[i+1] = centre of cell i, i = -1..n
+    for (int i = 0; i < n; ++i) cb[i + 1] = 0.5 * (f[i] + f[i + 1]);
+    const double L = f[n] - f[0];
+    if (periodic) {
+      cb[0] = cb[n] - L;
+      cb[n + 1] = cb[1] + L;
+    } else {
+      cb[0] = 2.0 * f[0] - cb[1];
+      cb[n + 1] = 2.0 * f[n] - cb[n];
+    }
+  };
+  std::vector<double> xcb, ycb;
+  centres(pb.xf, pb.per_x, xcb);
+  centres(pb.yf, pb.per_y, ycb);
+  auto faces = [&](const std::vector<double> &f, const std::vector<double> &cb,
+                   std::vector<double> &th, std::vector<double> &s) {
+    const int n = (int)f.size() - 1;
+    th.assign(n + 3, 0.5);
+    s.assign(n + 3, 0.0);
+    for (int k = 0; k <= n; ++k) {
+      const double cl = cb[k], cr = cb[k + 1]; // centres of cells k-1, k
+      th[k + 1] = (f[k] - cl) / (cr - cl);
+      s[k + 1] = h * c / (cr - cl);
+    }
+  };
+  auto cols = [&](const std::vector<double> &f, const std::vector<double> &cb,
+                  std::vector<double> &t, std::vector<double> &u) {
+    const int n = (int)f.size() - 1;
+    t.assign(n + 2, 0.0);
+    u.assign(n + 2, 0.0);
+    for (int i = 0; i < n; ++i) {
+      t[i + 1] = h * c / (cb[i + 2] - cb[i]);
+      u[i + 1] = pb.dt * c / (f[i + 1] - f[i]);
+    }
+  };
+  faces(pb.xf, xcb, pb.xfth, pb.xfs);
+  faces(pb.yf, ycb, pb.yfth, pb.yfs);
+  cols(pb.xf, xcb, pb.xct, pb.xcu);
+  cols(pb.yf, ycb, pb.yct, pb.ycu);
+  pb.ext[0] = (xcb[0] - xcb[1]) / (xcb[1] - xcb[2]);
+  pb.ext[1] = (xcb[nx + 1] - xcb[nx]) / (xcb[nx] - xcb[nx - 1]);
+  pb.ext[2] = (ycb[0] - ycb[1]) / (ycb[1] - ycb[2]);
+  pb.ext[3] = (ycb[ny + 1] - ycb[ny]) / (ycb[ny] - ycb[ny - 1]);
+  pb.volx.resize(nx);
+  pb.voly.resize(ny);
+  for (int i = 0; i < nx; ++i) pb.volx[i] = pb.xf[i + 1] - pb.xf[i];
+  for (int j = 0; j < ny; ++j) pb.voly[j] = pb.yf[j + 1] - pb.yf[j];
+  // segment of each boundary face by its centre coordinate
+  for (int s = 0; s < 4; ++s) {
+    const bool xs = s < 2;
+    const int n = xs ? ny : nx;
+    pb.segid[s].assign(n, 0);
+    if (per[s]) continue;
+    for (int k = 0; k < n; ++k) {
+      const double t = xs ? ycb[k + 1] : xcb[k + 1];
+      int g = find_seg(pb.bc[s], t);
+      if (g < 0) return fail(DVBE_ERR_INVALID_ARG, "a boundary face is not covered by any segment");
+      if (pb.bc[s][g].kind == DVBE_BC_PERIODIC)
+        return fail(DVBE_ERR_INVALID_ARG, "periodic segment on a non-periodic side");
+      pb.segid[s][k] = (unsigned char)g;
+    }
+    if ((pb.bc[s][0].kind == DVBE_BC_WALL_BOUNCEBACK || pb.bc[s][0].kind == DVBE_BC_WALL_DIFFUSE) &&
+        (xs ? nx : ny) < 2)
+      return fail(DVBE_ERR_INVALID_ARG, "walls need two cells normal to the side");
+  }
+  // transform coefficients (closed forms of Eqs. eq_trans_2 and the
+  // f_tilde / f_tilde^+ transforms of Sec 2.2)
+  const double tau = pb.tau, dt = pb.dt;
+  pb.c = c;
+  if (pb.user_scheme == DVBE_DUGKS) {
+    pb.a_phi = (2 * tau - h) / (2 * tau + dt);
+    pb.b_phi = 3 * h / (2 * tau + dt);
+  } else {
+    pb.a_phi = (2 * tau - dt) / (2 * tau + dt);
+    pb.b_phi = 2 * dt / (2 * tau + dt);
+  }
+  pb.a_tp = (2 * tau - dt) / (2 * tau + dt);
+  pb.b_tp = 2 * dt / (2 * tau + dt);
+  pb.p_face = 2 * tau / (2 * tau + h);
+  pb.q_face = h / (2 * tau + h);
+  pb.fd_nux = c * dt / (pb.xf[1] - pb.xf[0]);
+  pb.fd_nuy = c * dt / (pb.yf[1] - pb.yf[0]);
+  // storage layout: rows padded to 128 bytes
+  const int eb = elem_bytes(pb.store);
+  const int align = 128 / eb;
+  pb.pitch = ((nx + align - 1) / align) * align;
+  pb.plane = (long long)pb.pitch * ny;
+  pb.elem = eb;
+  return DVBE_OK;
+}
+
+// Device copy of the geometry tables in compute precision.
+template <typename Real>
+static void pack_tables(const Problem &pb, std::vector<char> &blob, size_t off[8]) {
+  const std::vector<double> *src[8] = {&pb.xfth, &pb.xfs, &pb.xct, &pb.xcu,
+                                       &pb.yfth, &pb.yfs, &pb.yct, &pb.ycu};
+  size_t pos = 0;
+  for (int q = 0; q < 8; ++q) {
+    off[q] = pos;
+    pos += ((src[q]->size() * sizeof(Real) + 255) / 256) * 256;
+  }
+  blob.assign(pos, 0);
+  for (int q = 0; q < 8; ++q) {
+    Real *d = (Real *)(blob.data() + off[q]);
+    for (size_t k = 0; k < src[q]->size(); ++k) d[k] = (Real)(*src[q])[k];
+  }
+}
+
+dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cudaStream_t s) {
+  std::vector<char> blob;
+  size_t off[8];
+  if (pb.store == ST_F64)
+    pack_tables<double>(pb, blob, off);
+  else
+    pack_tables<float>(pb, blob, off);
+  const size_t segbytes = 2 * (size_t)pb.ny + 2 * (size_t)pb.nx;
+  const size_t volbytes = sizeof(double) * (size_t)(pb.nx + pb.ny);
+  const size_t total = blob.size() + segbytes + volbytes + 256;
+  dp.blob = (char *)dmalloc(total, s);
+  if (!dp.blob) return fail(DVBE_ERR_OOM, "device allocation of geometry tables failed");
+  std::vector<char> host(total, 0);
+  memcpy(host.data(), blob.data(), blob.size());
+  size_t pos = blob.size();
+  size_t segoff[4];
+  for (int q = 0; q < 4; ++q) {
+    segoff[q] = pos;
+    memcpy(host.data() + pos, pb.segid[q].data(), pb.segid[q].size());
+    pos += pb.segid[q].size();
+  }
+  pos = ((pos + 7) / 8) * 8;
+  size_t voloff = pos;
+  memcpy(host.data() + pos, pb.volx.data(), sizeof(double) * pb.nx);
+  memcpy(host.data() + pos + sizeof(double) * pb.nx, pb.voly.data(), sizeof(double) * pb.ny);
+  cudaError_t e = cudaMemcpyAsync(dp.blob, host.data(), total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of geometry tables");
+  dp.volx = (double *)(dp.blob + voloff);
+  dp.voly = dp.volx + pb.nx;
+
+  memset(&a, 0, sizeof(a));
+  a.plane = pb.plane;
+  a.pitch = pb.pitch;
+  a.nx = pb.nx;
+  a.ny = pb.ny;
+  a.per_x = pb.per_x;
+  a.per_y = pb.per_y;
+  a.rho0 = pb.rho0;
+  a.a_phi = pb.a_phi;
+  a.b_phi = pb.b_phi;
+  a.a_tp = pb.a_tp;
+  a.b_tp = pb.b_tp;
+  a.p_face = pb.p_face;
+  a.q_face = pb.q_face;
+  a.dev_sigma = pb.sigma;
+  a.fd_nux = pb.fd_nux;
+  a.fd_nuy = pb.fd_nuy;
+  a.xfth = dp.blob + off[0];
+  a.xfs = dp.blob + off[1];
+  a.xct = dp.blob + off[2];
+  a.xcu = dp.blob + off[3];
+  a.yfth = dp.blob + off[4];
+  a.yfs = dp.blob + off[5];
+  a.yct = dp.blob + off[6];
+  a.ycu = dp.blob + off[7];
+  for (int q = 0; q < 4; ++q) {
+    a.ext[q] = pb.ext[q];
+    a.segid[q] = (const unsigned char *)(dp.blob + segoff[q]);
+    a.nseg[q] = (int)pb.bc[q].size();
+    for (size_t g = 0; g < pb.bc[q].size(); ++g) {
+      a.seg[q][g].kind = pb.bc[q][g].kind;
+      a.seg[q][g].rho = pb.bc[q][g].rho;
+      a.seg[q][g].ux = pb.bc[q][g].ux / pb.c;
+      a.seg[q][g].uy = pb.bc[q][g].uy / pb.c;
+    }
+  }
+  return DVBE_OK;
+}
+
+void set_strips(CaseArgs &a, int H) {
+  a.H = H;
+  a.strips_x = (a.nx + kStripCols - 1) / kStripCols;
+  a.strips_y = (a.ny + H - 1) / H;
+}
+
+FieldView view_of(const Problem &pb, void *f) {
+  FieldView v;
+  v.f = f;
+  v.plane = pb.plane;
+  v.pitch = pb.pitch;
+  v.nx = pb.nx;
+  v.ny = pb.ny;
+  v.store = pb.store;
+  v.rho0 = pb.rho0;
+  v.sigma = pb.sigma;
+  v.RT = pb.RT;
+  v.tau = pb.tau;
+  v.dt = pb.dt;
+  return v;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+  }
+  return n;
+}
+
+// Upload host float64 fields (each n doubles) into one staging allocation.
+dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStream_t s,
+                         double **out) {
+  double *d = (double *)dmalloc(sizeof(double) * n * count, s);
+  if (!d) return fail(DVBE_ERR_OOM, "device staging allocation failed");
+  for (int q = 0; q < count; ++q) {
+    cudaError_t e = cudaMemcpyAsync(d + q * n, src[q], sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      dfree(d, s);
+      return cuda_fail(e, "host to device copy");
+    }
+  }
+  *out = d;
+  return DVBE_OK;
+}
+
+} // namespace dvbe
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+
+struct dvbe_solver_ {
+  Problem pb;
+  DeviceProblem dp;
+  CaseArgs args;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned *flag = nullptr;
+  double *red = nullptr;  // reduction partials + 3 results
+  double *uprev = nullptr; // 2 * nx * ny (residual)
+  bool have_prev = false;
+  dvbe_launch launch{64, 4, 0, 0};
+  long long steps = 0, launches = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_len = 0;
+};
+
+static void drop_graphs(dvbe_solver s) {
+  for (int p = 0; p < 2; ++p)
+    if (s->graph[p]) {
+      cudaGraphExecDestroy(s->graph[p]);
+      s->graph[p] = nullptr;
+    }
+  s->graph_len = 0;
+}
+
+static FieldView cur_view(dvbe_solver s) { return view_of(s->pb, s->f[s->cur]); }
+
+extern "C" {
+
+const char *dvbe_last_error(void) { return g_err.c_str(); }
+
+const char *dvbe_version(void) { return "libdvbe 0.1 sm_103a"; }
+
+dvbe_status dvbe_set_allocator(dvbe_alloc_fn alloc, dvbe_free_fn free_, void *ctx) {
+  if ((alloc == nullptr) != (free_ == nullptr))
+    return fail(DVBE_ERR_INVALID_ARG, "allocator and free must both be set or both be NULL");
+  g_alloc = alloc;
+  g_free = free_;
+  g_ctx = ctx;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_d2q9(double RT, double *xi, double *w, int *opp) {
+  if (!(RT > 0) || !xi || !w || !opp) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  const double c = std::sqrt(3.0 * RT);
+  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  static const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  for (int a = 0; a < 9; ++a) {
+    xi[2 * a] = c * ex[a];
+    xi[2 * a + 1] = c * ey[a];
+    w[a] = a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    opp[a] = op[a];
+  }
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_mesh_create(int nx, int ny, const double *xf, const double *yf, dvbe_mesh *out) {
+  if (!out || !xf || !yf) return fail(DVBE_ERR_INVALID_ARG, "NULL pointer");
+  *out = nullptr;
+  if (nx < 2 || ny < 2) return fail(DVBE_ERR_INVALID_ARG, "nx and ny must be >= 2");
+  if ((long long)nx * ny > (1LL << 31)) return fail(DVBE_ERR_INVALID_ARG, "mesh too large");
+  for (int i = 0; i < nx; ++i)
+    if (!(xf[i + 1] > xf[i]) || !std::isfinite(xf[i + 1]))
+      return fail(DVBE_ERR_INVALID_ARG, "x faces must be finite and strictly increasing");
+  for (int j = 0; j < ny; ++j)
+    if (!(yf[j + 1] > yf[j]) || !std::isfinite(yf[j + 1]))
+      return fail(DVBE_ERR_INVALID_ARG, "y faces must be finite and strictly increasing");
+  dvbe_mesh m = new (std::nothrow) dvbe_mesh_;
+  if (!m) return fail(DVBE_ERR_OOM, "host allocation failed");
+  m->nx = nx;
+  m->ny = ny;
+  m->xf.assign(xf, xf + nx + 1);
+  m->yf.assign(yf, yf + ny + 1);
+  *out = m;
+  return DVBE_OK;
+}
+
+void dvbe_mesh_destroy(dvbe_mesh mesh) { delete mesh; }
+
+dvbe_status dvbe_mesh_geometry(dvbe_mesh m, double *xc, double *yc, double *vol) {
+  if (!m) return fail(DVBE_ERR_INVALID_ARG, "NULL mesh");
+  for (int i = 0; i < m->nx && xc; ++i) xc[i] = 0.5 * (m->xf[i] + m->xf[i + 1]);
+  for (int j = 0; j < m->ny && yc; ++j) yc[j] = 0.5 * (m->yf[j] + m->yf[j + 1]);
+  if (vol)
+    for (int j = 0; j < m->ny; ++j)
+      for (int i = 0; i < m->nx; ++i)
+        vol[(size_t)j * m->nx + i] = (m->xf[i + 1] - m->xf[i]) * (m->yf[j + 1] - m->yf[j]);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_faces_uniform(int n, double a, double b, double *out) {
+  if (n < 1 || !(b > a) || !out) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i <= n; ++i) out[i] = a + (b - a) * (double)i / (double)n;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_faces_tanh(int n, double a, double b, double beta, double *out) {
+  if (n < 1 || !(b > a) || !(beta > 0) || !out) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  const double tb = std::tanh(beta);
+  for (int i = 0; i <= n; ++i) {
+    const double s = (double)i / (double)n;
+    out[i] = a + (b - a) * 0.5 * (1.0 + std::tanh(beta * (2.0 * s - 1.0)) / tb);
+  }
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_faces_geometric(int n, double a, double d0, double ratio, double *out) {
+  if (n < 1 || !(d0 > 0) || !(ratio > 0) || !out) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i <= n; ++i)
+    out[i] = ratio == 1.0 ? a + d0 * i : a + d0 * (std::pow(ratio, (double)i) - 1.0) / (ratio - 1.0);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_dt_from_cfl(dvbe_mesh m, double RT, double cfl, double *dt) {
+  if (!m || !(RT > 0) || !(cfl > 0) || !dt) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  double dmin = INFINITY;
+  for (int i = 0; i < m->nx; ++i) dmin = std::min(dmin, m->xf[i + 1] - m->xf[i]);
+  for (int j = 0; j < m->ny; ++j) dmin = std::min(dmin, m->yf[j + 1] - m->yf[j]);
+  *dt = cfl * dmin / (std::sqrt(6.0) * std::sqrt(RT));
+  return DVBE_OK;
+}
+
+void dvbe_solver_destroy(dvbe_solver s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  drop_graphs(s);
+  dfree(s->f[0], s->stream);
+  dfree(s->f[1], s->stream);
+  dfree(s->flag, s->stream);
+  dfree(s->red, s->stream);
+  dfree(s->uprev, s->stream);
+  dfree(s->dp.blob, s->stream);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
+  if (!out) return fail(DVBE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  dvbe_solver s = new (std::nothrow) dvbe_solver_;
+  if (!s) return fail(DVBE_ERR_OOM, "host allocation failed");
+  dvbe_status st = build_problem(p, s->pb);
+  if (st != DVBE_OK) {
+    delete s;
+    return st;
+  }
+  if (p->cuda_stream) {
+    s->stream = (cudaStream_t)p->cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete s;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    s->own_stream = true;
+  }
+  st = upload_problem(s->pb, s->dp, s->args, s->stream);
+  const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
+  if (st == DVBE_OK) {
+    s->f[0] = dmalloc(fbytes, s->stream);
+    s->f[1] = dmalloc(fbytes, s->stream);
+    s->flag = (unsigned *)dmalloc(sizeof(unsigned), s->stream);
+    s->red = (double *)dmalloc(sizeof(double) * (kReduceBlocks * 3 + 3), s->stream);
+    if (!s->f[0] || !s->f[1] || !s->flag || !s->red) st = fail(DVBE_ERR_OOM, "device allocation of f_tilde failed");
+  }
+  if (st == DVBE_OK) {
+    cudaError_t e = cudaMemsetAsync(s->f[0], 0, fbytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, fbytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->flag, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = aux_fill_rest(cur_view(s), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "solver initialisation");
+    s->launches += 1;
+  }
+  if (st != DVBE_OK) {
+    dvbe_solver_destroy(s);
+    return st;
+  }
+  s->args.flag = s->flag;
+  set_strips(s->args, s->launch.strip_rows);
+  *out = s;
+  return DVBE_OK;
+}
+
+static dvbe_status after_init(dvbe_solver s, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  s->steps = 0;
+  s->have_prev = false;
+  unsigned z = 0;
+  e = cudaMemcpy(s->flag, &z, sizeof z, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_init_equilibrium(dvbe_solver s, const double *rho, const double *ux,
+                                  const double *uy) {
+  if (!s || !rho || !ux || !uy) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  const double *src[3] = {rho, ux, uy};
+  double *d = nullptr;
+  dvbe_status st = stage_fields(src, 3, n, s->stream, &d);
+  if (st != DVBE_OK) return st;
+  cudaError_t e = aux_init_eq(cur_view(s), d, d + n, d + 2 * n, s->stream);
+  s->launches += 1;
+  st = after_init(s, e, "init_equilibrium");
+  dfree(d, s->stream);
+  return st;
+}
+
+dvbe_status dvbe_init_chapman_enskog(dvbe_solver s, const double *rho, const double *ux,
+                                     const double *uy, const double *const *dd) {
+  if (!s || !rho || !ux || !uy || !dd) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  for (int q = 0; q < 9; ++q)
+    if (!dd[q]) return fail(DVBE_ERR_INVALID_ARG, "NULL derivative array");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  const double *src[12] = {rho, ux, uy, dd[0], dd[1], dd[2], dd[3], dd[4], dd[5], dd[6], dd[7], dd[8]};
+  double *d = nullptr;
+  dvbe_status st = stage_fields(src, 12, n, s->stream, &d);
+  if (st != DVBE_OK) return st;
+  const double *dp[9];
+  for (int q = 0; q < 9; ++q) dp[q] = d + (3 + q) * n;
+  cudaError_t e = aux_init_ce(cur_view(s), d, d + n, d + 2 * n, dp, s->stream);
+  s->launches += 1;
+  st = after_init(s, e, "init_chapman_enskog");
+  dfree(d, s->stream);
+  return st;
+}
+
+dvbe_status dvbe_init_f(dvbe_solver s, const double *ft) {
+  if (!s || !ft) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  double *d = (double *)dmalloc(sizeof(double) * n, s->stream);
+  if (!d) return fail(DVBE_ERR_OOM, "device staging allocation failed");
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < 9 && e == cudaSuccess; ++a) {
+    e = cudaMemcpyAsync(d, ft + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = aux_set_field(cur_view(s), a, d, s->stream);
+    s->launches += 1;
+  }
+  dvbe_status st = after_init(s, e, "init_f");
+  dfree(d, s->stream);
+  return st;
+}
+
+dvbe_status dvbe_get_f(dvbe_solver s, double *ft) {
+  if (!s || !ft) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  double *d = (double *)dmalloc(sizeof(double) * n, s->stream);
+  if (!d) return fail(DVBE_ERR_OOM, "device staging allocation failed");
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < 9 && e == cudaSuccess; ++a) {
+    e = aux_get_field(cur_view(s), a, d, s->stream);
+    s->launches += 1;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ft + a * n, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(d, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_f");
+  return DVBE_OK;
+}
+
+static cudaError_t launch_one(dvbe_solver s) {
+  s->args.fin = s->f[s->cur];
+  s->args.fout = s->f[1 - s->cur];
+  cudaError_t e = launch_step(s->pb.store, s->pb.kernel, s->args, s->launch.blocks,
+                              s->launch.warps_per_block, s->stream);
+  s->cur ^= 1;
+  s->steps += 1;
+  s->launches += 1;
+  return e;
+}
+
+static cudaError_t capture(dvbe_solver s, int parity, int len) {
+  cudaGraph_t g = nullptr;
+  const int saved_cur = s->cur;
+  const long long saved_steps = s->steps, saved_l = s->launches;
+  s->cur = parity;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < len; ++k) {
+    cudaError_t x = launch_one(s);
+    if (x != cudaSuccess && le == cudaSuccess) le = x;
+  }
+  e = cudaStreamEndCapture(s->stream, &g);
+  s->cur = saved_cur;
+  s->steps = saved_steps;
+  s->launches = saved_l;
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+dvbe_status dvbe_step_async(dvbe_solver s, long long nsteps) {
+  if (!s || nsteps < 0) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  cudaError_t e = cudaSuccess;
+  int chunk = s->launch.graph_chunk;
+  if (chunk > 0) chunk += chunk & 1; // even, so a replay keeps the buffer parity
+  if (chunk > 0 && nsteps >= chunk) {
+    if (s->graph_len != chunk) {
+      drop_graphs(s);
+      for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = capture(s, p, chunk);
+      if (e != cudaSuccess) {
+        drop_graphs(s);
+        return cuda_fail(e, "graph capture");
+      }
+      s->graph_len = chunk;
+    }
+    while (nsteps >= chunk && e == cudaSuccess) {
+      e = cudaGraphLaunch(s->graph[s->cur], s->stream);
+      s->steps += chunk;
+      s->launches += chunk;
+      nsteps -= chunk;
+    }
+  }
+  for (long long k = 0; k < nsteps && e == cudaSuccess; ++k) e = launch_one(s);
+  if (e != cudaSuccess) return cuda_fail(e, "step launch");
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_sync(dvbe_solver s) {
+  if (!s) return fail(DVBE_ERR_INVALID_ARG, "NULL solver");
+  unsigned flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, s->flag, sizeof flag, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronise");
+  if (flag) return fail(DVBE_ERR_DIVERGED, "non-finite or non-positive density met");
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_step(dvbe_solver s, long long nsteps) {
+  dvbe_status st = dvbe_step_async(s, nsteps);
+  if (st != DVBE_OK) return st;
+  return dvbe_sync(s);
+}
+
+dvbe_status dvbe_step_count(dvbe_solver s, long long *n) {
+  if (!s || !n) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  *n = s->steps;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_get_moments(dvbe_solver s, double *rho, double *ux, double *uy) {
+  if (!s || !rho || !ux || !uy) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  double *d = (double *)dmalloc(sizeof(double) * 3 * n, s->stream);
+  if (!d) return fail(DVBE_ERR_OOM, "device staging allocation failed");
+  cudaError_t e = aux_moments(cur_view(s), d, d + n, d + 2 * n, s->stream);
+  s->launches += 1;
+  double *dst[3] = {rho, ux, uy};
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(dst[q], d + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(d, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_moments");
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_conserved(dvbe_solver s, double out[3]) {
+  if (!s || !out) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  double *res = s->red + kReduceBlocks * 3;
+  cudaError_t e = aux_conserved(cur_view(s), s->dp.volx, s->dp.voly, s->red, res, s->stream);
+  s->launches += 2;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "conserved");
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_residual(dvbe_solver s, double *r) {
+  if (!s || !r) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  if (!s->uprev) {
+    s->uprev = (double *)dmalloc(sizeof(double) * 2 * n, s->stream);
+    if (!s->uprev) return fail(DVBE_ERR_OOM, "device allocation failed");
+  }
+  double *res = s->red + kReduceBlocks * 3;
+  cudaError_t e = aux_velocity_error(cur_view(s), s->uprev, s->uprev + n, 1, s->red, res, s->stream);
+  s->launches += 2;
+  double out[3];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "residual");
+  *r = s->have_prev ? std::sqrt(out[0]) / std::sqrt(out[1]) : INFINITY;
+  s->have_prev = true;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_l2_error_u(dvbe_solver s, const double *ua, const double *va, double *eu) {
+  if (!s || !ua || !va || !eu) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)s->pb.nx * s->pb.ny;
+  const double *src[2] = {ua, va};
+  double *d = nullptr;
+  dvbe_status st = stage_fields(src, 2, n, s->stream, &d);
+  if (st != DVBE_OK) return st;
+  double *res = s->red + kReduceBlocks * 3;
+  cudaError_t e = aux_velocity_error(cur_view(s), d, d + n, 0, s->red, res, s->stream);
+  s->launches += 2;
+  double out[3];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(d, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "l2_error_u");
+  *eu = std::sqrt(out[0]) / std::sqrt(out[1]);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_get_launch(dvbe_solver s, dvbe_launch *out) {
+  if (!s || !out) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  *out = s->launch;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in) {
+  if (!s || !in) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  if (in->strip_rows < 1 || in->warps_per_block < 1 || in->warps_per_block > 8 || in->blocks < 0 ||
+      in->graph_chunk < 0)
+    return fail(DVBE_ERR_INVALID_ARG, "strip_rows >= 1, warps_per_block in 1..8, blocks >= 0");
+  dvbe_status st = dvbe_sync(s);
+  if (st != DVBE_OK && st != DVBE_ERR_DIVERGED) return st;
+  s->launch = *in;
+  set_strips(s->args, in->strip_rows);
+  drop_graphs(s);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
+  if (!s || steps < 1) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
+  void *backup = dmalloc(fbytes, s->stream);
+  if (!backup) return fail(DVBE_ERR_OOM, "device allocation failed");
+  cudaError_t e = cudaMemcpyAsync(backup, s->f[s->cur], fbytes, cudaMemcpyDeviceToDevice, s->stream);
+  const int saved_cur = s->cur;
+  const long long saved_steps = s->steps;
+  const dvbe_launch saved = s->launch;
+  std::vector<dvbe_launch> cand;
+  const int rows[] = {16, 32, 64, 128, 256};
+  const int wpbs[] = {2, 4, 8};
+  for (int H : rows)
+    for (int w : wpbs) {
+      cand.push_back({H, w, 0, 0});
+      cand.push_back({H, w, sm_count() * (32 / w), 0});
+    }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = INFINITY;
+  dvbe_launch bestc = saved;
+  for (auto &c : cand) {
+    if (e != cudaSuccess) break;
+    if (c.strip_rows > 2 * s->pb.ny && c.strip_rows > 16) continue;
+    s->launch = c;
+    s->launch.graph_chunk = 0;
+    set_strips(s->args, c.strip_rows);
+    e = launch_one(s); // warm-up
+    if (e != cudaSuccess) break;
+    cudaEventRecord(e0, s->stream);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_one(s);
+    cudaEventRecord(e1, s->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / steps < best) {
+      best = ms / steps;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->cur = saved_cur;
+  s->steps = saved_steps;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->f[s->cur], backup, fbytes, cudaMemcpyDeviceToDevice, s->stream);
+  unsigned z = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->flag, &z, sizeof z, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(backup, s->stream);
+  bestc.graph_chunk = saved.graph_chunk;
+  s->launch = bestc;
+  set_strips(s->args, bestc.strip_rows);
+  drop_graphs(s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (best_ms) *best_ms = best;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch, long long *plane,
+                              int *elem_bytes_) {
+  if (!s) return fail(DVBE_ERR_INVALID_ARG, "NULL solver");
+  if (ptr) *ptr = s->f[s->cur];
+  if (pitch) *pitch = s->pb.pitch;
+  if (plane) *plane = s->pb.plane;
+  if (elem_bytes_) *elem_bytes_ = s->pb.elem;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_launch_count(dvbe_solver s, long long *count) {
+  if (!s || !count) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  *count = s->launches;
+  return DVBE_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,97 @@
+// Internal declarations shared by the host side of libdvbe and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dvbe.h"
+
+namespace dvbe {
+
+// Device storage of f_tilde (matches dvbe_precision).
+enum StoreMode { ST_F64 = 0, ST_F32 = 1, ST_F32_DEV = 2, ST_F16_DEV = 3, ST_BF16_DEV = 4 };
+
+// Kernel variants: the DUGKS flux (Sec 2.2), the BKG flux in finite-volume
+// form (Eq. bkg_fv with the face values of Eq. f_left generalised to
+// stretched meshes), and BKG as the Lax-Wendroff stencil (Eq. bkgfd).
+enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2 };
+
+// Lanes per warp minus the two halo columns: output columns per warp row.
+constexpr int kStripCols = 30;
+
+struct SegParam {
+  int kind;   // dvbe_bc_kind
+  double rho; // wall: unused; inflow: free-stream density
+  double ux;  // wall velocity / free-stream velocity, divided by the lattice speed c
+  double uy;
+};
+
+// Everything one fused step of one case needs.  Plain data so that it can be
+// a __grid_constant__ kernel parameter (single solver) or an element of a
+// device array (batched form).
+struct CaseArgs {
+  const void *fin;
+  void *fout;
+  long long plane; // elements per field
+  int pitch;       // elements per row
+  int nx, ny;
+  int per_x, per_y;
+  int strips_x, strips_y, H; // strip decomposition: 30 columns x H rows per warp
+
+  double rho0;
+  double a_phi, b_phi;   // phi = a delta + b delta_eq   (DUGKS: f_bar^+, BKG: f_tilde^+)
+  double a_tp, b_tp;     // f_tilde^+ = a delta + b delta_eq (DUGKS update)
+  double p_face, q_face; // DUGKS face: f = p f_bar + q f_eq
+  double dev_sigma;      // deviation storage: s_alpha = dev_sigma w_alpha rho0
+  double fd_nux, fd_nuy; // BKG-FD: c dt / dx, c dt / dy (uniform meshes)
+
+  // Geometry tables in compute precision (double for F64, float otherwise).
+  const void *xfth, *xfs; // [nx+3]: x-face k at k+1: theta_k, h c / (xc_k - xc_{k-1})
+  const void *xct, *xcu;  // [nx+2]: column i at i+1: h c / (xc_{i+1} - xc_{i-1}), dt c / dx_i
+  const void *yfth, *yfs; // [ny+3]
+  const void *yct, *ycu;  // [ny+2]
+  double ext[4];          // ghost extrapolation factor per side (W E S N)
+  const unsigned char *segid[4]; // W, E: [ny]; S, N: [nx]
+  int nseg[4];
+  SegParam seg[4][DVBE_MAX_SEGMENTS];
+
+  unsigned int *flag; // bit 0: divergence seen
+};
+
+// Step launchers (one translation unit per storage mode).
+cudaError_t launch_step(int store, int scheme, const CaseArgs &a, int blocks, int warps_per_block,
+                        cudaStream_t s);
+cudaError_t launch_step_batch(int store, int scheme, const CaseArgs *d_cases,
+                              const long long *d_prefix, int ncases, long long nitems,
+                              unsigned long long *d_queue, int blocks, int warps_per_block,
+                              cudaStream_t s);
+
+// Auxiliary kernels (aux_kernels.cu).  Host-side arrays are double, unpitched.
+struct FieldView {
+  void *f; // storage base
+  long long plane;
+  int pitch, nx, ny, store;
+  double rho0, sigma, RT, tau, dt;
+};
+cudaError_t aux_init_eq(const FieldView &v, const double *d_rho, const double *d_ux,
+                        const double *d_uy, cudaStream_t s);
+cudaError_t aux_init_ce(const FieldView &v, const double *d_rho, const double *d_ux,
+                        const double *d_uy, const double *const *d_deriv, cudaStream_t s);
+// f_tilde = w_alpha rho0 (fluid at rest)
+cudaError_t aux_fill_rest(const FieldView &v, cudaStream_t s);
+// one field alpha: double [ny][nx] <-> storage
+cudaError_t aux_set_field(const FieldView &v, int alpha, const double *d_src, cudaStream_t s);
+cudaError_t aux_get_field(const FieldView &v, int alpha, double *d_dst, cudaStream_t s);
+cudaError_t aux_moments(const FieldView &v, double *d_rho, double *d_ux, double *d_uy,
+                        cudaStream_t s);
+// Deterministic FP64 reductions; partials must hold kReduceBlocks * 3 doubles,
+// result 3 doubles.
+constexpr int kReduceBlocks = 296;
+cudaError_t aux_conserved(const FieldView &v, const double *d_vol_x, const double *d_vol_y,
+                          double *d_partials, double *d_out, cudaStream_t s);
+// sums |u - ref|^2 and |ref|^2 (mode 0: ref = given arrays, E_u); mode 1:
+// residual against d_ua/d_va = previous velocity, which is then overwritten.
+cudaError_t aux_velocity_error(const FieldView &v, double *d_ua, double *d_va, int mode,
+                               double *d_partials, double *d_out, cudaStream_t s);
+
+} // namespace dvbe

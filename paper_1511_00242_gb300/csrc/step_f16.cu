@@ -1,0 +1,16 @@
+// Step kernels with FP32 arithmetic and 16-bit deviation storage (FP16, BF16).
+#include "step_kernel.cuh"
+
+namespace dvbe {
+cudaError_t launch_step_f16(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
+                            cudaStream_t s) {
+  if (store == ST_F16_DEV) return launch_step_impl<ST_F16_DEV>(scheme, a, blocks, wpb, s);
+  return launch_step_impl<ST_BF16_DEV>(scheme, a, blocks, wpb, s);
+}
+cudaError_t launch_batch_f16(int store, int scheme, const CaseArgs *c, const long long *p, int n,
+                             long long ni, unsigned long long *q, int blocks, int wpb,
+                             cudaStream_t s) {
+  if (store == ST_F16_DEV) return launch_batch_impl<ST_F16_DEV>(scheme, c, p, n, ni, q, blocks, wpb, s);
+  return launch_batch_impl<ST_BF16_DEV>(scheme, c, p, n, ni, q, blocks, wpb, s);
+}
+} // namespace dvbe
