@@ -42,7 +42,7 @@ typedef enum {
   DVBE_ERR_OOM = 3,         /* device or host allocation failed              */
   DVBE_ERR_CUDA = 4,        /* a CUDA runtime call failed                    */
   DVBE_ERR_DIVERGED = 5,    /* a non-finite or non-positive density was met  */
-  DVBE_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait ran out       */
+  DVBE_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out            */
   DVBE_ERR_UNSUPPORTED = 7  /* valid request this build does not provide     */
 } dvbe_status;
 

@@ -38,8 +38,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _flags():
+    """NVCC flags; DVBE_MIN_BLOCKS (environment) sets the step kernel's
+    occupancy target, i.e. its register cap (1 -> up to 255 registers,
+    2 -> 128)."""
+    mb = os.environ.get("DVBE_MIN_BLOCKS", "1")
+    return NVCC_FLAGS + ["-DDVBE_MIN_BLOCKS=%d" % int(mb)]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags = " ".join(_flags())
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "dvbe.h")]
     objs, jobs = [], []
     for src in SOURCES:
@@ -47,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
+            cmd = [nvcc()] + _flags() + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -70,6 +82,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed: " + " ".join(cmd))
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 

@@ -20,6 +20,7 @@ struct dvbe_batch_ {
   std::vector<DeviceProblem> dp;
   std::vector<CaseArgs> args;
   std::vector<void *> f[2];
+  std::vector<CUtensorMap> tm[2][2]; // [buffer parity][main, wrap][case]
   unsigned *flags = nullptr;
   // per buffer parity: case arguments grouped by scheme (DUGKS first), and
   // the strip prefix of each group
@@ -67,6 +68,8 @@ static dvbe_status batch_tables(dvbe_batch b) {
     for (int k = 0; k < b->n; ++k) {
       const int c = b->order[k];
       tab[k] = b->args[c];
+      tab[k].tm_main = b->tm[p][0][c];
+      tab[k].tm_wrap = b->tm[p][1][c];
       tab[k].fin = b->f[p][c];
       tab[k].fout = b->f[1 - p][c];
       tab[k].flag = b->flags + c;
@@ -128,6 +131,8 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
   b->args.resize(ncases);
   b->f[0].assign(ncases, nullptr);
   b->f[1].assign(ncases, nullptr);
+  for (int p = 0; p < 2; ++p)
+    for (int m = 0; m < 2; ++m) b->tm[p][m].resize(ncases);
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete b;
@@ -146,6 +151,7 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
       for (int p = 0; p < 2; ++p) {
         b->f[p][c] = dmalloc(fbytes, b->stream);
         if (!b->f[p][c]) st = fail(DVBE_ERR_OOM, "device allocation of f_tilde failed");
+        if (st == DVBE_OK) st = make_tensor_maps(b->pb[c], b->f[p][c], &b->tm[p][0][c], &b->tm[p][1][c]);
       }
     }
     if (st == DVBE_OK) {
@@ -260,6 +266,7 @@ dvbe_status dvbe_batch_case_status(dvbe_batch b, int c) {
   cudaError_t e = cudaMemcpyAsync(&flag, b->flags + c, sizeof flag, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch status");
+  if (flag & 2u) return fail(DVBE_ERR_TIMEOUT, "a bounded wait in the step kernel ran out");
   if (flag) return fail(DVBE_ERR_DIVERGED, "case diverged");
   return DVBE_OK;
 }

@@ -46,6 +46,9 @@ FieldView view_of(const Problem &pb, void *f);
 int sm_count();
 dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStream_t s,
                          double **out);
+// Tensor maps of one f_tilde buffer for the step kernel's row pipeline.
+dvbe_status make_tensor_maps(const Problem &pb, void *f, CUtensorMap *main_map,
+                             CUtensorMap *wrap_map);
 
 cudaError_t launch_step_f64(int scheme, const CaseArgs &a, int blocks, int wpb, cudaStream_t s);
 cudaError_t launch_step_f32(int store, int scheme, const CaseArgs &a, int blocks, int wpb,

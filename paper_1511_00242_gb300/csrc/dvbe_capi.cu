@@ -251,10 +251,11 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   pb.q_face = h / (2 * tau + h);
   pb.fd_nux = c * dt / (pb.xf[1] - pb.xf[0]);
   pb.fd_nuy = c * dt / (pb.yf[1] - pb.yf[0]);
-  // storage layout: rows padded to 128 bytes
+  // storage layout: rows padded to 128 bytes and at least 64 elements, so a
+  // staged row box (at most 40 elements) always fits inside a row
   const int eb = elem_bytes(pb.store);
   const int align = 128 / eb;
-  pb.pitch = ((nx + align - 1) / align) * align;
+  pb.pitch = std::max(((nx + align - 1) / align) * align, 64);
   pb.plane = (long long)pb.pitch * ny;
   pb.elem = eb;
   return DVBE_OK;
@@ -369,6 +370,64 @@ FieldView view_of(const Problem &pb, void *f) {
   return v;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+dvbe_status make_tensor_maps(const Problem &pb, void *f, CUtensorMap *main_map,
+                             CUtensorMap *wrap_map) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(DVBE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  CUtensorMapDataType dt;
+  switch (pb.store) {
+    case ST_F64:
+      dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+      break;
+    case ST_F16_DEV:
+      dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+      break;
+    case ST_BF16_DEV:
+      dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+      break;
+    default:
+      dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  }
+  const int es = pb.elem;
+  // the step kernel stages 34 (FP64), 36 (FP32) or 40 (16-bit) columns per row
+  const cuuint32_t W = es == 8 ? 34 : (es == 4 ? 36 : 40);
+  const cuuint64_t dims[3] = {(cuuint64_t)pb.pitch, (cuuint64_t)pb.ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)pb.pitch * es, (cuuint64_t)pb.plane * es};
+  const cuuint32_t box_main[3] = {W, 1, 9};
+  const cuuint32_t box_wrap[3] = {(cuuint32_t)(16 / es), 1, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(main_map, dt, 3, f, dims, strides, box_main, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r == CUDA_SUCCESS)
+    r = enc(wrap_map, dt, 3, f, dims, strides, box_wrap, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(DVBE_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return DVBE_OK;
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -420,6 +479,7 @@ struct dvbe_solver_ {
   long long steps = 0, launches = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_len = 0;
+  CUtensorMap tm[2][2]; // [buffer][main, wrap]
 };
 
 static void drop_graphs(dvbe_solver s) {
@@ -572,6 +632,8 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
     s->red = (double *)dmalloc(sizeof(double) * (kReduceBlocks * 3 + 3), s->stream);
     if (!s->f[0] || !s->f[1] || !s->flag || !s->red) st = fail(DVBE_ERR_OOM, "device allocation of f_tilde failed");
   }
+  for (int p = 0; p < 2 && st == DVBE_OK; ++p)
+    st = make_tensor_maps(s->pb, s->f[p], &s->tm[p][0], &s->tm[p][1]);
   if (st == DVBE_OK) {
     cudaError_t e = cudaMemsetAsync(s->f[0], 0, fbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, fbytes, s->stream);
@@ -671,6 +733,8 @@ dvbe_status dvbe_get_f(dvbe_solver s, double *ft) {
 }
 
 static cudaError_t launch_one(dvbe_solver s) {
+  s->args.tm_main = s->tm[s->cur][0];
+  s->args.tm_wrap = s->tm[s->cur][1];
   s->args.fin = s->f[s->cur];
   s->args.fout = s->f[1 - s->cur];
   cudaError_t e = launch_step(s->pb.store, s->pb.kernel, s->args, s->launch.blocks,
@@ -736,7 +800,8 @@ dvbe_status dvbe_sync(dvbe_solver s) {
   cudaError_t e = cudaMemcpyAsync(&flag, s->flag, sizeof flag, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronise");
-  if (flag) return fail(DVBE_ERR_DIVERGED, "non-finite or non-positive density met");
+  if (flag & 2u) return fail(DVBE_ERR_TIMEOUT, "a bounded wait in the step kernel ran out");
+  if (flag & 1u) return fail(DVBE_ERR_DIVERGED, "non-finite or non-positive density met");
   return DVBE_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host side of libdvbe and its kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,11 @@ struct SegParam {
 // a __grid_constant__ kernel parameter (single solver) or an element of a
 // device array (batched form).
 struct CaseArgs {
+  // Tensor maps of the input buffer, viewed as [9][ny][pitch]: tm_main with
+  // a box of one row of the staged columns x 9 fields, tm_wrap with a
+  // 16-byte box for periodic wrap columns.
+  CUtensorMap tm_main;
+  CUtensorMap tm_wrap;
   const void *fin;
   void *fout;
   long long plane; // elements per field

@@ -30,6 +30,11 @@
 
 #include "internal.h"
 
+// Blocks of 256 threads the step kernel must fit per SM; sets its register cap.
+#ifndef DVBE_MIN_BLOCKS
+#define DVBE_MIN_BLOCKS 1
+#endif
+
 namespace dvbe {
 namespace dev {
 
@@ -102,7 +107,14 @@ template <typename T> __device__ __forceinline__ void store_real(T *p, float v) 
 }
 
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Single precision: hardware approximation refined by one Newton-Raphson
+// step r <- r (2 - x r), within about one ulp of 1/x.
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  const float e = fmaf(-x, r, 1.0f);
+  return fmaf(r, e, r);
+}
 
 // Weight class of a direction: 0 rest, 1 axis, 2 diagonal.
 __host__ __device__ constexpr int WCLS(int a) { return a == 0 ? 0 : (a <= 4 ? 1 : 2); }
@@ -116,8 +128,8 @@ template <typename Real> struct K {
 };
 
 template <int ST, typename Real, typename T>
-__device__ __forceinline__ Real load_delta(const T *p, int a, const K<Real> &k) {
-  Real v = to_real(*p);
+__device__ __forceinline__ Real decode(T raw, int a, const K<Real> &k) {
+  Real v = to_real(raw);
   if constexpr (StoreT<ST>::DEV)
     return v * k.sc[WCLS(a)];
   else
@@ -239,50 +251,188 @@ template <int SCHEME> __host__ __device__ constexpr bool needy(int a) {
   return SCHEME == SC_DUGKS ? true : EY(a) != 0;
 }
 
+// ---- TMA / mbarrier primitives (inline PTX) ---------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// 3-d tiled bulk tensor copy global -> shared, completion on an mbarrier.
+__device__ __forceinline__ void tma_load3(uint32_t dst, const void *tmap, int x, int y, int z,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+template <typename T> __device__ __forceinline__ T lds(uint32_t addr);
+template <> __device__ __forceinline__ double lds<double>(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+template <> __device__ __forceinline__ float lds<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+template <> __device__ __forceinline__ __half lds<__half>(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return __ushort_as_half(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 lds<__nv_bfloat16>(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return __ushort_as_bfloat16(v);
+}
+
+// Predicated global stores (no branch around the store).
+__device__ __forceinline__ void st_pred(double *p, double v, bool on) {
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.f64 [%0], %1; }" ::"l"(p), "d"(v),
+               "r"((int)on)
+               : "memory");
+}
+__device__ __forceinline__ void st_pred(float *p, float v, bool on) {
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.f32 [%0], %1; }" ::"l"(p), "f"(v),
+               "r"((int)on)
+               : "memory");
+}
+__device__ __forceinline__ void st_pred(__half *p, float v, bool on) {
+  const unsigned short b = __half_as_ushort(__float2half_rn(v));
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.b16 [%0], %1; }" ::"l"(p), "h"(b),
+               "r"((int)on)
+               : "memory");
+}
+__device__ __forceinline__ void st_pred(__nv_bfloat16 *p, float v, bool on) {
+  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.b16 [%0], %1; }" ::"l"(p), "h"(b),
+               "r"((int)on)
+               : "memory");
+}
+
+// Waits longer than this many polls are treated as a failure: the warp sets
+// bit 1 of the case flag and abandons its work (the host reports a timeout).
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Shared-memory geometry of one warp's row pipeline for element size ES.
+template <int ES> struct Pipe {
+  // columns per staged row: covers the 32 lanes' columns from a 16-byte
+  // aligned start (the tensor copy needs x * ES to be a multiple of 16)
+  static constexpr int W = ES == 8 ? 34 : (ES == 4 ? 36 : 40);
+  static constexpr int WW = 16 / ES; // columns of the periodic-wrap copies
+  static constexpr int NS = 5;       // stages: rows j, j+1 held, three in flight
+  static constexpr int MAINB = ((9 * W * ES + 127) / 128) * 128;
+  static constexpr int WRAPB = 256; // each wrap copy (9 * 16 bytes) at a 128-byte boundary
+  static constexpr int STAGEB = MAINB + 2 * WRAPB;
+  static constexpr int WARPB = NS * STAGEB + 128; // + NS mbarriers, 128-byte multiple
+};
+
 // ---- the strip ---------------------------------------------------------------
 
 template <int SCHEME, int ST> struct Strip {
   using S = StoreT<ST>;
   using Real = typename S::Real;
   using T = typename S::T;
+  using P = Pipe<(int)sizeof(T)>;
   static constexpr bool DUG = SCHEME == SC_DUGKS;
   static constexpr bool FD = SCHEME == SC_BKG_FD;
+  static constexpr int ES = (int)sizeof(T);
 
   const CaseArgs &A;
   K<Real> k;
-  int lane, i, lc, nx, ny;
-  bool per_x, per_y, touchW, touchE, out_lane;
-  Real a_phi, b_phi, a_tp, b_tp, p_face, q_face;
+  int lane, i, nx, ny, i0, xs;
+  bool valid, per_x, per_y, touchW, touchE, out_lane, wrapW, wrapE;
+  Real a_phi, b_phi, p_face, q_face;
   // x-face coefficients of this lane: right part of its west face, left part
   // of its east face; tangential / update factors of its column.
   Real cR[3], cL[3], tR0, tL0, txc, cxu;
   // BKG-FD stencil factors
   Real kx1, kx2, ky1, ky2, kxy;
   int segS, segN;
-  const T *fin;
   T *fout;
   bool bad;
+  // row pipeline of this warp
+  uint32_t sbase, bbase, txbytes;
+  uint32_t lds_off; // byte offset of this lane's first value inside a stage
+  uint32_t lds_stride;
+  // Fetches are issued and waited for in order; islot / cslot are the stages
+  // of the next issue / wait and cphase holds the parity to wait for on each
+  // stage.  These persist across the strips a warp processes.
+  int islot, cslot;
+  uint32_t cphase;
+  int nfetch, nissued, nwaited; // of the current strip
+  int Fa;                       // logical row of fetch 0
+  bool timeout;
 
-  __device__ __forceinline__ Strip(const CaseArgs &args, int lane_) : A(args), lane(lane_) {}
+  __device__ __forceinline__ Strip(const CaseArgs &args, int lane_, uint32_t sbase_)
+      : A(args), lane(lane_), sbase(sbase_) {
+    bbase = sbase + P::NS * P::STAGEB;
+    islot = 0;
+    cslot = 0;
+    cphase = 0;
+    bad = false;
+    timeout = false;
+  }
+
+  __device__ __forceinline__ void init_barriers() {
+    if (lane == 0) {
+      for (int s = 0; s < P::NS; ++s) mbar_init(bbase + 8 * s, 1);
+      fence_mbar_init();
+    }
+    __syncwarp();
+  }
 
   __device__ __forceinline__ void setup(int sx) {
     nx = A.nx;
     ny = A.ny;
     per_x = A.per_x;
     per_y = A.per_y;
-    const int i0 = sx * kStripCols;
+    i0 = sx * kStripCols;
     i = i0 - 1 + lane;
-    if (i >= 0 && i < nx)
-      lc = i;
-    else if (per_x && i == -1)
-      lc = nx - 1;
-    else if (per_x && i == nx)
-      lc = 0;
-    else
-      lc = -1;
+    valid = (i >= 0 && i < nx) || (per_x && (i == -1 || i == nx));
     touchW = !per_x && i0 == 0;
     touchE = !per_x && i0 + kStripCols >= nx;
+    wrapW = per_x && i0 == 0;
+    wrapE = per_x && i0 + kStripCols >= nx;
     out_lane = lane >= 1 && lane <= kStripCols && i < nx;
+    // staged columns: [xs, xs + W) with xs the aligned start at or left of i0 - 1
+    const int al = 16 / ES;
+    xs = (i0 - 1 >= 0) ? ((i0 - 1) / al) * al : -al;
+    lds_off = (uint32_t)((i - xs) * ES);
+    lds_stride = (uint32_t)(P::W * ES);
+    if (wrapW && i == -1) { // column nx-1 from the west wrap copy
+      const int xw = ((nx - 1) / al) * al;
+      lds_off = (uint32_t)(P::MAINB + (nx - 1 - xw) * ES);
+      lds_stride = (uint32_t)(P::WW * ES);
+    }
+    if (wrapE && i == nx) { // column 0 from the east wrap copy
+      lds_off = (uint32_t)(P::MAINB + P::WRAPB);
+      lds_stride = (uint32_t)(P::WW * ES);
+    }
+    txbytes = 9u * P::W * ES + (wrapW ? 9u * 16u : 0u) + (wrapE ? 9u * 16u : 0u);
     const int ic = min(max(i, -1), nx);
     const Real *xfth = (const Real *)A.xfth, *xfs = (const Real *)A.xfs;
     const Real *xct = (const Real *)A.xct, *xcu = (const Real *)A.xcu;
@@ -310,8 +460,6 @@ template <int SCHEME, int ST> struct Strip {
     }
     a_phi = Real(A.a_phi);
     b_phi = Real(A.b_phi);
-    a_tp = Real(A.a_tp);
-    b_tp = Real(A.b_tp);
     p_face = Real(A.p_face);
     q_face = Real(A.q_face);
     if constexpr (FD) {
@@ -322,33 +470,81 @@ template <int SCHEME, int ST> struct Strip {
       ky2 = Real(0.5) * nuy * nuy;
       kxy = Real(0.25) * nux * nuy;
     }
-    fin = (const T *)A.fin;
     fout = (T *)A.fout;
   }
 
-  // Row r (0 <= r < ny): load, cell stage, x ghosts.
-  __device__ __forceinline__ void produce(int r, Real (&phi)[9], Real (&tp)[9]) {
-    if (lc >= 0) {
-      const T *p = fin + (long long)r * A.pitch + lc;
-      Real d[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) d[a] = load_delta<ST, Real>(p + a * A.plane, a, k);
-      Real rp, rho, Ux, Uy;
-      moments(d, k.rho0, rp, rho, Ux, Uy);
-      bad |= !(rho > Real(0) && rho < Real(1e30));
-      Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        Real de = deq_of<Real>(a, rp, rho, Ux, Uy, u15);
-        phi[a] = a_phi * d[a] + b_phi * de;
-        if constexpr (DUG) tp[a] = a_tp * d[a] + b_tp * de;
+  // ---- row pipeline: fetch number q of this strip is logical row Fa + q
+  __device__ __forceinline__ void issue() {
+    if (timeout) return;
+    if (lane == 0) {
+      const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
+      const int r = wrapr(Fa + nissued);
+      mbar_expect_tx(bar, txbytes);
+      tma_load3(dst, &A.tm_main, xs, r, 0, bar);
+      if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, ((nx - 1) / (16 / ES)) * (16 / ES), r, 0, bar);
+      if (wrapE) tma_load3(dst + P::MAINB + P::WRAPB, &A.tm_wrap, 0, r, 0, bar);
+    }
+    islot = islot + 1 == P::NS ? 0 : islot + 1;
+    ++nissued;
+  }
+
+  // Wait (bounded) for the next fetch in order; returns its stage address.
+  __device__ __forceinline__ uint32_t wait() {
+    const uint32_t st = sbase + cslot * P::STAGEB;
+    if (!timeout) {
+      const uint32_t bar = bbase + 8 * cslot, par = (cphase >> cslot) & 1u;
+      uint32_t n = 0;
+      bool late = false;
+      while (!mbar_try_wait(bar, par)) {
+        if (++n >= kSpinLimit) {
+          late = true;
+          break;
+        }
       }
-    } else {
+      timeout = __any_sync(kFull, late);
+      if (!timeout) ++nwaited;
+    }
+    cphase ^= 1u << cslot;
+    cslot = cslot + 1 == P::NS ? 0 : cslot + 1;
+    return st;
+  }
+
+  // The oldest held stage is no longer read: reuse it for the next fetch.
+  __device__ __forceinline__ void release() {
+    if (nissued < nfetch) {
+      __syncwarp();
+      if (lane == 0) fence_proxy_async();
+      issue();
+    }
+  }
+
+  __device__ __forceinline__ void read_row(uint32_t stage, Real (&d)[9]) {
+    const uint32_t base = stage + lds_off;
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        phi[a] = Real(0);
-        if constexpr (DUG) tp[a] = Real(0);
-      }
+    for (int a = 0; a < 9; ++a) d[a] = decode<ST, Real>(lds<T>(base + a * lds_stride), a, k);
+  }
+
+  // Cell stage of a staged row r, then the x ghosts:
+  // phi = a d + b w (rho' + rho P) with b w folded per weight class.
+  __device__ __forceinline__ void stage_row(int r, uint32_t stage, Real (&phi)[9]) {
+    Real d[9];
+    read_row(stage, d);
+    Real rp, rho, Ux, Uy;
+    moments(d, k.rho0, rp, rho, Ux, Uy);
+    bad |= valid && !(rho > Real(0) && rho < Real(1e30));
+    const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
+    Real cr[3], cp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const Real bw = b_phi * Real(c == 0 ? WGT(0) : (c == 1 ? WGT(1) : WGT(5)));
+      cr[c] = bw * rho;
+      cp[c] = bw * rp;
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
+      const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
+      phi[a] = a_phi * d[a] + (cr[WCLS(a)] * Pq + cp[WCLS(a)]);
     }
     if (touchW || touchE) ghost_x(r, phi);
   }
@@ -388,18 +584,21 @@ template <int SCHEME, int ST> struct Strip {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       if (!needx<SCHEME>(a)) continue;
-      Real Lp = P0[a] * cL[EX(a) + 1];
-      Real Rp = P0[a] * cR[EX(a) + 1];
       if (EY(a) != 0) {
-        Real dy = Pp[a] - Pm[a];
-        Lp -= Real(EY(a)) * tL * dy;
-        Rp -= Real(EY(a)) * tR * dy;
+        const Real dy = Pp[a] - Pm[a];
+        const Real Lp = P0[a] * cL[EX(a) + 1] - Real(EY(a)) * tL * dy;
+        const Real in = __shfl_up_sync(kFull, Lp, 1) - Real(EY(a)) * tR * dy;
+        F[a] = P0[a] * cR[EX(a) + 1] + in;
+      } else {
+        const Real Lp = P0[a] * cL[EX(a) + 1];
+        F[a] = P0[a] * cR[EX(a) + 1] + __shfl_up_sync(kFull, Lp, 1);
       }
-      F[a] = __shfl_up_sync(kFull, Lp, 1) + Rp;
     }
-    if (!per_x && (i == 0 || i == nx)) {
-      const int side = i == 0 ? 0 : 1;
-      face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
+    if (touchW || touchE) { // warp-uniform test first
+      if (i == 0 || i == nx) {
+        const int side = i == 0 ? 0 : 1;
+        face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
+      }
     }
     if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, p_face, q_face);
   }
@@ -435,25 +634,43 @@ template <int SCHEME, int ST> struct Strip {
     if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, p_face, q_face);
   }
 
-  // One row of the finite-volume update.
-  __device__ __forceinline__ void update_fv(int j, const Real (&T0)[9], const Real (&FW)[9],
-                                            const Real (&FS)[9], const Real (&FN)[9]) {
-    const Real cyu = ((const Real *)A.ycu)[j + 1];
-    Real v[9];
+  __device__ __forceinline__ void store_row(int j, const Real (&v)[9]) {
+    T *p = fout + (long long)j * A.pitch + min(max(i, 0), nx - 1);
+    const long long plane = A.plane;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      v[a] = T0[a];
+      const Real x = StoreT<ST>::DEV ? v[a] * k.isc[WCLS(a)] : v[a] + k.wr[WCLS(a)];
+      st_pred(p, x, out_lane);
+      p += plane;
+    }
+  }
+
+  // One row of the finite-volume update.  DUGKS needs f_tilde^+ of the cell,
+  // recomputed from the staged deviations d and phi = f_bar^+ as
+  // f_tilde^+ = (4 phi - d) / 3 (the two transforms of Sec 2.2 combined).
+  __device__ __forceinline__ void update_fv(int j, uint32_t stage, const Real (&Pb)[9],
+                                            const Real (&FW)[9], const Real (&FS)[9],
+                                            const Real (&FN)[9]) {
+    const Real cyu = ((const Real *)A.ycu)[j + 1];
+    Real v[9];
+    if constexpr (DUG) {
+      Real d[9];
+      read_row(stage, d);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) v[a] = (Real(4) * Pb[a] - d[a]) * Real(1.0 / 3.0);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) v[a] = Pb[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
       if (EX(a) != 0) {
         Real FE = __shfl_down_sync(kFull, FW[a], 1);
         v[a] -= Real(EX(a)) * cxu * (FE - FW[a]);
       }
       if (EY(a) != 0) v[a] -= Real(EY(a)) * cyu * (FN[a] - FS[a]);
     }
-    if (out_lane) {
-      T *p = fout + (long long)j * A.pitch + i;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) store_delta<ST, Real>(p + a * A.plane, a, v[a], k);
-    }
+    store_row(j, v);
   }
 
   // One row of the Lax-Wendroff stencil (Eqs. bkgfd, central_schemes).
@@ -485,24 +702,27 @@ template <int SCHEME, int ST> struct Strip {
       }
       v[a] = M;
     }
-    if (out_lane) {
-      T *p = fout + (long long)j * A.pitch + i;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) store_delta<ST, Real>(p + a * A.plane, a, v[a], k);
-    }
+    store_row(j, v);
   }
 
-  // One full row: produce row j+1 into Pc (unless have_next), faces, update.
-  // Pa, Pb, Pc = phi of rows j-1, j, j+1 (Tb, Tc: f_tilde^+ of rows j, j+1).
-  __device__ __forceinline__ void row(int j, bool have_next, Real (&Pa)[9], Real (&Pb)[9],
-                                      Real (&Pc)[9], Real (&Tb)[9], Real (&Tc)[9], Real (&FS)[9]) {
+  // Logical row L (-1 .. ny) is stored (periodic wrap) unless it is a ghost row.
+  __device__ __forceinline__ bool stored(int L) const { return per_y || (L >= 0 && L < ny); }
+  __device__ __forceinline__ int wrapr(int L) const { return L < 0 ? L + ny : (L >= ny ? L - ny : L); }
+
+  // One full row j: phi of row j+1 into Pc (unless have_next), faces, update.
+  // Pa, Pb, Pc = phi of rows j-1, j, j+1; stj / stn = stages holding rows j
+  // and j+1 (stj is released at the end of the row).
+  __device__ __forceinline__ void row(int j, int jend, bool have_next, Real (&Pa)[9],
+                                      Real (&Pb)[9], Real (&Pc)[9], Real (&FS)[9], uint32_t &stj,
+                                      uint32_t &stn) {
     if (!have_next) {
-      if (j + 1 < ny)
-        produce(j + 1, Pc, Tc);
-      else if (per_y)
-        produce(0, Pc, Tc);
-      else
+      if (stored(j + 1)) {
+        stn = wait();
+        stage_row(wrapr(j + 1), stn, Pc);
+        if (j + 1 == jend) release(); // only phi of this row is needed
+      } else {
         ghost_row(3, Pb, Pa, Pc);
+      }
     }
     if constexpr (FD) {
       update_fd(j, Pa, Pb, Pc);
@@ -510,64 +730,113 @@ template <int SCHEME, int ST> struct Strip {
       Real FW[9], FN[9];
       xface(j, Pa, Pb, Pc, FW);
       yface(j + 1, Pb, Pc, FN);
-      update_fv(j, DUG ? Tb : Pb, FW, FS, FN);
+      update_fv(j, stj, Pb, FW, FS, FN);
 #pragma unroll
       for (int a = 0; a < 9; ++a) FS[a] = FN[a];
     }
+    release();
+    stj = stn;
   }
 
   __device__ __forceinline__ void run(int sx, int sy) {
     setup(sx);
     const int j0 = sy * A.H;
     const int jend = min(j0 + A.H, ny);
-    Real P0[9], P1[9], P2[9], T0[9], T1[9], T2[9], FS[9];
+    const bool ghost_bottom = j0 == 0 && !per_y;
+    Fa = ghost_bottom ? 0 : j0 - 1;
+    const int Fb = stored(jend) ? jend : jend - 1;
+    nfetch = Fb - Fa + 1;
+    nissued = 0;
+    nwaited = 0;
+    while (nissued < nfetch && nissued < P::NS) issue();
+    Real P0[9], P1[9], P2[9], FS[9];
+    uint32_t stj, stn = 0;
     bool have_next;
-    // prologue: rows j0-1 (P0) and j0 (P1) [and j0+1 (P2) at a ghost bottom]
-    if (j0 == 0 && !per_y) {
-      produce(0, P1, T1);
-      produce(1, P2, T2);
+    if (ghost_bottom) {
+      stj = wait();
+      stage_row(0, stj, P1);
+      stn = wait();
+      stage_row(1, stn, P2);
       ghost_row(2, P1, P2, P0);
       have_next = true;
     } else {
-      produce(j0 == 0 ? ny - 1 : j0 - 1, P0, T0);
-      produce(j0, P1, T1);
+      stage_row(wrapr(j0 - 1), wait(), P0);
+      release(); // row j0-1 contributes phi only
+      stj = wait();
+      stage_row(wrapr(j0), stj, P1);
       have_next = false;
     }
     if constexpr (!FD) yface(j0, P0, P1, FS);
-    // rows, unrolled by three so that the phi / f_tilde^+ registers rotate
-    // without copies
+    // rows, unrolled by three so that the phi registers rotate without copies
     int j = j0;
     while (true) {
       if (j >= jend) break;
-      row(j, have_next, P0, P1, P2, T1, T2, FS);
+      row(j, jend, have_next, P0, P1, P2, FS, stj, stn);
       have_next = false;
       if (++j >= jend) break;
-      row(j, false, P1, P2, P0, T2, T0, FS);
+      row(j, jend, false, P1, P2, P0, FS, stj, stn);
       if (++j >= jend) break;
-      row(j, false, P2, P0, P1, T0, T1, FS);
+      row(j, jend, false, P2, P0, P1, FS, stj, stn);
       ++j;
+    }
+  }
+
+  // After a timed-out wait: give the copies still in flight a bounded time
+  // to land before the warp leaves (their shared memory must stay valid).
+  // Fetches nwaited .. nissued-1 are outstanding; the first of them was due
+  // on the stage before cslot.
+  __device__ __forceinline__ void drain() {
+    int s = cslot - 1 < 0 ? P::NS - 1 : cslot - 1;
+    uint32_t ph = cphase ^ (1u << s); // undo the flip of the timed-out wait
+    for (int q = nwaited; q < nissued; ++q) {
+      uint32_t n = 0;
+      while (!mbar_try_wait(bbase + 8 * s, (ph >> s) & 1u) && ++n < (1u << 16)) {
+      }
+      ph ^= 1u << s;
+      s = s + 1 == P::NS ? 0 : s + 1;
     }
   }
 };
 
 template <int SCHEME, int ST>
-__global__ void __launch_bounds__(256) k_step(const __grid_constant__ CaseArgs A) {
+__global__ void __launch_bounds__(256, DVBE_MIN_BLOCKS) k_step(const __grid_constant__ CaseArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using P = Pipe<(int)sizeof(typename StoreT<ST>::T)>;
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long nitems = (long long)A.strips_x * A.strips_y;
-  Strip<SCHEME, ST> s(A, lane);
-  s.bad = false;
-  for (long long it = gw; it < nitems; it += nw) s.run((int)(it % A.strips_x), (int)(it / A.strips_x));
+  Strip<SCHEME, ST> s(A, lane, smem_u32(smem) + wib * P::WARPB);
+  s.init_barriers();
+  for (long long it = gw; it < nitems; it += nw) {
+    s.run((int)(it % A.strips_x), (int)(it / A.strips_x));
+    if (__any_sync(kFull, s.timeout)) break;
+  }
+  if (__any_sync(kFull, s.timeout)) {
+    s.drain();
+    if (lane == 0) atomicOr(A.flag, 2u);
+  }
   if (__any_sync(kFull, s.bad) && lane == 0) atomicOr(A.flag, 1u);
 }
 
 // Batched form: warps take strips of all cases from one queue.
 template <int SCHEME, int ST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
     k_step_batch(const CaseArgs *__restrict__ cases, const long long *__restrict__ prefix,
                  int ncases, long long nitems, unsigned long long *queue) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using P = Pipe<(int)sizeof(typename StoreT<ST>::T)>;
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const uint32_t sb = smem_u32(smem) + wib * P::WARPB;
+  int pipe_slot = 0;       // stage of this warp's next fetch
+  uint32_t pipe_phase = 0; // parity to wait for on each stage
+  bool timeout = false;
+  {
+    Strip<SCHEME, ST> s0(cases[0], lane, sb);
+    s0.init_barriers();
+  }
   while (true) {
     long long item = 0;
     if (lane == 0) item = (long long)atomicAdd(queue, 1ull);
@@ -588,26 +857,46 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) dead = *(volatile unsigned *)A.flag;
     if (__shfl_sync(kFull, dead, 0)) continue;
     const long long local = item - prefix[lo];
-    Strip<SCHEME, ST> s(A, lane);
-    s.bad = false;
+    Strip<SCHEME, ST> s(A, lane, sb);
+    s.islot = pipe_slot;
+    s.cslot = pipe_slot;
+    s.cphase = pipe_phase;
     s.run((int)(local % A.strips_x), (int)(local / A.strips_x));
+    pipe_slot = s.cslot;
+    pipe_phase = s.cphase;
     if (__any_sync(kFull, s.bad) && lane == 0) atomicOr(A.flag, 1u);
+    if (__any_sync(kFull, s.timeout)) {
+      s.drain();
+      if (lane == 0) atomicOr(A.flag, 2u);
+      timeout = true;
+      break;
+    }
   }
+  (void)timeout;
 }
 
 } // namespace dev
 
+template <int ST> constexpr int warp_smem() {
+  return dev::Pipe<(int)sizeof(typename dev::StoreT<ST>::T)>::WARPB;
+}
+
+template <typename K> cudaError_t allow_smem(K kern, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 template <int ST>
 cudaError_t launch_step_impl(int scheme, const CaseArgs &a, int blocks, int wpb, cudaStream_t s) {
   dim3 block(32 * wpb);
+  const int smem = wpb * warp_smem<ST>();
   const long long nitems = (long long)a.strips_x * a.strips_y;
   if (blocks <= 0) blocks = (int)((nitems + wpb - 1) / wpb);
-  if (scheme == SC_DUGKS)
-    dev::k_step<SC_DUGKS, ST><<<blocks, block, 0, s>>>(a);
-  else if (scheme == SC_BKG_FV)
-    dev::k_step<SC_BKG_FV, ST><<<blocks, block, 0, s>>>(a);
-  else
-    dev::k_step<SC_BKG_FD, ST><<<blocks, block, 0, s>>>(a);
+  auto kern = scheme == SC_DUGKS ? dev::k_step<SC_DUGKS, ST>
+                                 : (scheme == SC_BKG_FV ? dev::k_step<SC_BKG_FV, ST> : dev::k_step<SC_BKG_FD, ST>);
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -616,17 +905,20 @@ cudaError_t launch_batch_impl(int scheme, const CaseArgs *d_cases, const long lo
                               int ncases, long long nitems, unsigned long long *d_queue,
                               int blocks, int wpb, cudaStream_t s) {
   dim3 block(32 * wpb);
+  const int smem = wpb * warp_smem<ST>();
   auto kern = scheme == SC_DUGKS ? dev::k_step_batch<SC_DUGKS, ST> : dev::k_step_batch<SC_BKG_FV, ST>;
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
   if (blocks <= 0) {
     // persistent grid: as many blocks as fit on the GPU at once
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x, smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     blocks = (per_sm > 0 ? per_sm : 1) * sms;
   }
-  kern<<<blocks, block, 0, s>>>(d_cases, d_prefix, ncases, nitems, d_queue);
+  kern<<<blocks, block, smem, s>>>(d_cases, d_prefix, ncases, nitems, d_queue);
   return cudaGetLastError();
 }
 
