@@ -258,6 +258,9 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   pb.pitch = std::max(((nx + align - 1) / align) * align, 64);
   pb.plane = (long long)pb.pitch * ny;
   pb.elem = eb;
+  // the step kernel addresses f_tilde with 32-bit element offsets
+  if (9 * pb.plane >= (1LL << 32))
+    return fail(DVBE_ERR_UNSUPPORTED, "mesh too large for one solver (9 x cells must stay below 2^32)");
   return DVBE_OK;
 }
 

@@ -33,7 +33,7 @@ struct SegParam {
 struct CaseArgs {
   // Tensor maps of the input buffer, viewed as [9][ny][pitch]: tm_main with
   // a box of one row of the staged columns x 9 fields, tm_wrap with a
-  // 16-byte box for periodic wrap columns.
+  // 16-byte x 9-field box for periodic wrap columns.
   CUtensorMap tm_main;
   CUtensorMap tm_wrap;
   const void *fin;

@@ -127,25 +127,21 @@ template <typename Real> struct K {
   Real isc[3]; // 1 / storage scale
 };
 
+// Deviation-storage modes compute on d = f_tilde - w rho0 (decode: d = s x);
+// absolute-storage modes compute on f_tilde itself, i.e. with reference
+// density 0 (decode: identity), which saves the offset add per value.
 template <int ST, typename Real, typename T>
 __device__ __forceinline__ Real decode(T raw, int a, const K<Real> &k) {
   Real v = to_real(raw);
   if constexpr (StoreT<ST>::DEV)
     return v * k.sc[WCLS(a)];
   else
-    return v - k.wr[WCLS(a)];
+    return v;
 }
 
-template <int ST, typename Real, typename T>
-__device__ __forceinline__ void store_delta(T *p, int a, Real d, const K<Real> &k) {
-  if constexpr (StoreT<ST>::DEV)
-    store_real(p, d * k.isc[WCLS(a)]);
-  else
-    store_real(p, d + k.wr[WCLS(a)]);
-}
-
-// delta_eq_alpha = f_eq_alpha - w rho0 = w (rho' + rho P(e.U)) with
-// P = 3 eU + 4.5 eU^2 - 1.5 |U|^2 and U = u / c (Eq. equilibrium, c_s^2 = c^2/3).
+// delta_eq_alpha = f_eq_alpha - w rref = w (rho' + rho P(e.U)) with rho' =
+// rho - rref, P = 3 eU + 4.5 eU^2 - 1.5 |U|^2 and U = u / c (Eq. equilibrium,
+// c_s^2 = c^2/3).  rref is rho0 for deviation storage and 0 otherwise.
 template <typename Real>
 __device__ __forceinline__ Real deq_of(int a, Real rp, Real rho, Real Ux, Real Uy, Real u15) {
   Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
@@ -345,9 +341,15 @@ template <int ES> struct Pipe {
   static constexpr int WW = 16 / ES; // columns of the periodic-wrap copies
   static constexpr int NS = 5;       // stages: rows j, j+1 held, three in flight
   static constexpr int MAINB = ((9 * W * ES + 127) / 128) * 128;
-  static constexpr int WRAPB = 256; // each wrap copy (9 * 16 bytes) at a 128-byte boundary
+  // periodic-wrap copies: a 9 x 16-byte box each (fields packed 16 bytes
+  // apart); every tensor-copy destination sits on a 128-byte boundary
+  static constexpr int WRAPB = 256;
   static constexpr int STAGEB = MAINB + 2 * WRAPB;
   static constexpr int WARPB = NS * STAGEB + 128; // + NS mbarriers, 128-byte multiple
+  // tensor-copy destinations (stage, main box, wrap copies) need 128-byte alignment
+  static_assert(MAINB % 128 == 0 && WRAPB % 128 == 0 && STAGEB % 128 == 0 && WARPB % 128 == 0,
+                "shared-memory layout must keep tensor-copy destinations 128-byte aligned");
+  static_assert(9 * W * ES <= MAINB && 9 * 16 <= WRAPB && NS * 8 <= 128, "buffer sizes");
 };
 
 // ---- the strip ---------------------------------------------------------------
@@ -363,7 +365,7 @@ template <int SCHEME, int ST> struct Strip {
 
   const CaseArgs &A;
   K<Real> k;
-  int lane, i, nx, ny, i0, xs;
+  int lane, i, nx, ny, i0, xs, xwrapW;
   bool valid, per_x, per_y, touchW, touchE, out_lane, wrapW, wrapE;
   Real a_phi, b_phi, p_face, q_face;
   // x-face coefficients of this lane: right part of its west face, left part
@@ -377,7 +379,7 @@ template <int SCHEME, int ST> struct Strip {
   // row pipeline of this warp
   uint32_t sbase, bbase, txbytes;
   uint32_t lds_off; // byte offset of this lane's first value inside a stage
-  uint32_t lds_stride;
+  bool wrap_lane;   // reads a periodic wrap copy (fields 16 bytes apart)
   // Fetches are issued and waited for in order; islot / cslot are the stages
   // of the next issue / wait and cphase holds the parity to wait for on each
   // stage.  These persist across the strips a warp processes.
@@ -422,17 +424,19 @@ template <int SCHEME, int ST> struct Strip {
     const int al = 16 / ES;
     xs = (i0 - 1 >= 0) ? ((i0 - 1) / al) * al : -al;
     lds_off = (uint32_t)((i - xs) * ES);
-    lds_stride = (uint32_t)(P::W * ES);
-    if (wrapW && i == -1) { // column nx-1 from the west wrap copy
-      const int xw = ((nx - 1) / al) * al;
-      lds_off = (uint32_t)(P::MAINB + (nx - 1 - xw) * ES);
-      lds_stride = (uint32_t)(P::WW * ES);
+    // periodic wrap columns come from the wrap copies: column nx-1 for the
+    // west halo lane, column 0 for the east halo lane
+    wrap_lane = false;
+    if (wrapW && i == -1) {
+      lds_off = (uint32_t)(P::MAINB + (nx - 1 - ((nx - 1) / (16 / ES)) * (16 / ES)) * ES);
+      wrap_lane = true;
     }
-    if (wrapE && i == nx) { // column 0 from the east wrap copy
+    if (wrapE && i == nx) {
       lds_off = (uint32_t)(P::MAINB + P::WRAPB);
-      lds_stride = (uint32_t)(P::WW * ES);
+      wrap_lane = true;
     }
     txbytes = 9u * P::W * ES + (wrapW ? 9u * 16u : 0u) + (wrapE ? 9u * 16u : 0u);
+    xwrapW = ((nx - 1) / (16 / ES)) * (16 / ES);
     const int ic = min(max(i, -1), nx);
     const Real *xfth = (const Real *)A.xfth, *xfs = (const Real *)A.xfs;
     const Real *xct = (const Real *)A.xct, *xcu = (const Real *)A.xcu;
@@ -450,13 +454,15 @@ template <int SCHEME, int ST> struct Strip {
     const int icc = min(max(i, 0), nx - 1);
     segS = per_y ? 0 : A.segid[2][icc];
     segN = per_y ? 0 : A.segid[3][icc];
-    k.rho0 = Real(A.rho0);
+    // reference density of the arithmetic: rho0 for deviation storage, 0 for
+    // absolute storage
+    k.rho0 = StoreT<ST>::DEV ? Real(A.rho0) : Real(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       double w = c == 0 ? WGT(0) : (c == 1 ? WGT(1) : WGT(5));
-      k.wr[c] = Real(w * A.rho0);
-      k.sc[c] = Real(A.dev_sigma * w * A.rho0);
-      k.isc[c] = Real(1.0 / (A.dev_sigma * w * A.rho0));
+      k.wr[c] = Real(0);
+      k.sc[c] = StoreT<ST>::DEV ? Real(A.dev_sigma * w * A.rho0) : Real(1);
+      k.isc[c] = StoreT<ST>::DEV ? Real(1.0 / (A.dev_sigma * w * A.rho0)) : Real(1);
     }
     a_phi = Real(A.a_phi);
     b_phi = Real(A.b_phi);
@@ -475,13 +481,12 @@ template <int SCHEME, int ST> struct Strip {
 
   // ---- row pipeline: fetch number q of this strip is logical row Fa + q
   __device__ __forceinline__ void issue() {
-    if (timeout) return;
-    if (lane == 0) {
+    if (lane == 0 && !timeout) {
       const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
       const int r = wrapr(Fa + nissued);
       mbar_expect_tx(bar, txbytes);
       tma_load3(dst, &A.tm_main, xs, r, 0, bar);
-      if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, ((nx - 1) / (16 / ES)) * (16 / ES), r, 0, bar);
+      if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, xwrapW, r, 0, bar);
       if (wrapE) tma_load3(dst + P::MAINB + P::WRAPB, &A.tm_wrap, 0, r, 0, bar);
     }
     islot = islot + 1 == P::NS ? 0 : islot + 1;
@@ -489,19 +494,19 @@ template <int SCHEME, int ST> struct Strip {
   }
 
   // Wait (bounded) for the next fetch in order; returns its stage address.
+  // A lane whose wait runs out stops waiting from then on; the warp checks
+  // the flag once per strip.
   __device__ __forceinline__ uint32_t wait() {
     const uint32_t st = sbase + cslot * P::STAGEB;
     if (!timeout) {
       const uint32_t bar = bbase + 8 * cslot, par = (cphase >> cslot) & 1u;
       uint32_t n = 0;
-      bool late = false;
       while (!mbar_try_wait(bar, par)) {
         if (++n >= kSpinLimit) {
-          late = true;
+          timeout = true;
           break;
         }
       }
-      timeout = __any_sync(kFull, late);
       if (!timeout) ++nwaited;
     }
     cphase ^= 1u << cslot;
@@ -518,17 +523,24 @@ template <int SCHEME, int ST> struct Strip {
     }
   }
 
-  __device__ __forceinline__ void read_row(uint32_t stage, Real (&d)[9]) {
+  template <bool INT> __device__ __forceinline__ void read_row(uint32_t stage, Real (&d)[9]) {
     const uint32_t base = stage + lds_off;
+    if (!INT && (wrapW || wrapE)) { // warp-uniform: only the strips at a periodic x edge
 #pragma unroll
-    for (int a = 0; a < 9; ++a) d[a] = decode<ST, Real>(lds<T>(base + a * lds_stride), a, k);
+      for (int a = 0; a < 9; ++a)
+        d[a] = decode<ST, Real>(lds<T>(base + a * (wrap_lane ? 16u : (uint32_t)(P::W * ES))), a, k);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) d[a] = decode<ST, Real>(lds<T>(base + a * P::W * ES), a, k);
+    }
   }
 
   // Cell stage of a staged row r, then the x ghosts:
   // phi = a d + b w (rho' + rho P) with b w folded per weight class.
+  template <bool INT>
   __device__ __forceinline__ void stage_row(int r, uint32_t stage, Real (&phi)[9]) {
     Real d[9];
-    read_row(stage, d);
+    read_row<INT>(stage, d);
     Real rp, rho, Ux, Uy;
     moments(d, k.rho0, rp, rho, Ux, Uy);
     bad |= valid && !(rho > Real(0) && rho < Real(1e30));
@@ -546,7 +558,7 @@ template <int SCHEME, int ST> struct Strip {
       const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
       phi[a] = a_phi * d[a] + (cr[WCLS(a)] * Pq + cp[WCLS(a)]);
     }
-    if (touchW || touchE) ghost_x(r, phi);
+    if (!INT && (touchW || touchE)) ghost_x(r, phi);
   }
 
   __device__ __forceinline__ void ghost_x(int r, Real (&phi)[9]) {
@@ -577,6 +589,7 @@ template <int SCHEME, int ST> struct Strip {
   }
 
   // Flux values of the x-face west of this lane's cell at row j.
+  template <bool INT>
   __device__ __forceinline__ void xface(int j, const Real (&Pm)[9], const Real (&P0)[9],
                                         const Real (&Pp)[9], Real (&F)[9]) {
     const Real tyc = ((const Real *)A.yct)[j + 1];
@@ -594,7 +607,7 @@ template <int SCHEME, int ST> struct Strip {
         F[a] = P0[a] * cR[EX(a) + 1] + __shfl_up_sync(kFull, Lp, 1);
       }
     }
-    if (touchW || touchE) { // warp-uniform test first
+    if (!INT && (touchW || touchE)) { // warp-uniform test first
       if (i == 0 || i == nx) {
         const int side = i == 0 ? 0 : 1;
         face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
@@ -605,6 +618,7 @@ template <int SCHEME, int ST> struct Strip {
 
   // Flux values of the y-face kf (between rows kf-1 and kf) at this column;
   // Pl = phi of row kf-1, Pu = phi of row kf.
+  template <bool INT>
   __device__ __forceinline__ void yface(int kf, const Real (&Pl)[9], const Real (&Pu)[9],
                                         Real (&F)[9]) {
     const Real th = ((const Real *)A.yfth)[kf + 1], s = ((const Real *)A.yfs)[kf + 1];
@@ -627,7 +641,7 @@ template <int SCHEME, int ST> struct Strip {
       }
       F[a] = own;
     }
-    if (!per_y && (kf == 0 || kf == ny)) {
+    if (!INT && !per_y && (kf == 0 || kf == ny)) {
       const int side = kf == 0 ? 2 : 3;
       face_bc<Real>(A.seg[side][side == 2 ? segS : segN], 0, side == 2 ? -1 : 1, k.rho0, F);
     }
@@ -635,19 +649,20 @@ template <int SCHEME, int ST> struct Strip {
   }
 
   __device__ __forceinline__ void store_row(int j, const Real (&v)[9]) {
-    T *p = fout + (long long)j * A.pitch + min(max(i, 0), nx - 1);
-    const long long plane = A.plane;
+    // element offsets fit in 32 bits: buffers are limited to 2^31 elements
+    const unsigned off = (unsigned)j * (unsigned)A.pitch + (unsigned)min(max(i, 0), nx - 1);
+    const unsigned plane = (unsigned)A.plane;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const Real x = StoreT<ST>::DEV ? v[a] * k.isc[WCLS(a)] : v[a] + k.wr[WCLS(a)];
-      st_pred(p, x, out_lane);
-      p += plane;
+      const Real x = StoreT<ST>::DEV ? v[a] * k.isc[WCLS(a)] : v[a];
+      st_pred(fout + (off + a * plane), x, out_lane);
     }
   }
 
   // One row of the finite-volume update.  DUGKS needs f_tilde^+ of the cell,
   // recomputed from the staged deviations d and phi = f_bar^+ as
   // f_tilde^+ = (4 phi - d) / 3 (the two transforms of Sec 2.2 combined).
+  template <bool INT>
   __device__ __forceinline__ void update_fv(int j, uint32_t stage, const Real (&Pb)[9],
                                             const Real (&FW)[9], const Real (&FS)[9],
                                             const Real (&FN)[9]) {
@@ -655,7 +670,7 @@ template <int SCHEME, int ST> struct Strip {
     Real v[9];
     if constexpr (DUG) {
       Real d[9];
-      read_row(stage, d);
+      read_row<INT>(stage, d);
 #pragma unroll
       for (int a = 0; a < 9; ++a) v[a] = (Real(4) * Pb[a] - d[a]) * Real(1.0 / 3.0);
     } else {
@@ -711,14 +726,17 @@ template <int SCHEME, int ST> struct Strip {
 
   // One full row j: phi of row j+1 into Pc (unless have_next), faces, update.
   // Pa, Pb, Pc = phi of rows j-1, j, j+1; stj / stn = stages holding rows j
-  // and j+1 (stj is released at the end of the row).
+  // and j+1 (stj is released at the end of the row).  INT: the strip touches
+  // no boundary (all its columns and rows j0-1 .. jend are inner cells), so
+  // the ghost, wrap and boundary-face code is compiled out.
+  template <bool INT>
   __device__ __forceinline__ void row(int j, int jend, bool have_next, Real (&Pa)[9],
                                       Real (&Pb)[9], Real (&Pc)[9], Real (&FS)[9], uint32_t &stj,
                                       uint32_t &stn) {
-    if (!have_next) {
-      if (stored(j + 1)) {
+    if (INT || !have_next) {
+      if (INT || stored(j + 1)) {
         stn = wait();
-        stage_row(wrapr(j + 1), stn, Pc);
+        stage_row<INT>(INT ? j + 1 : wrapr(j + 1), stn, Pc);
         if (j + 1 == jend) release(); // only phi of this row is needed
       } else {
         ghost_row(3, Pb, Pa, Pc);
@@ -728,9 +746,9 @@ template <int SCHEME, int ST> struct Strip {
       update_fd(j, Pa, Pb, Pc);
     } else {
       Real FW[9], FN[9];
-      xface(j, Pa, Pb, Pc, FW);
-      yface(j + 1, Pb, Pc, FN);
-      update_fv(j, stj, Pb, FW, FS, FN);
+      xface<INT>(j, Pa, Pb, Pc, FW);
+      yface<INT>(j + 1, Pb, Pc, FN);
+      update_fv<INT>(j, stj, Pb, FW, FS, FN);
 #pragma unroll
       for (int a = 0; a < 9; ++a) FS[a] = FN[a];
     }
@@ -738,47 +756,54 @@ template <int SCHEME, int ST> struct Strip {
     stj = stn;
   }
 
-  __device__ __forceinline__ void run(int sx, int sy) {
-    setup(sx);
-    const int j0 = sy * A.H;
-    const int jend = min(j0 + A.H, ny);
-    const bool ghost_bottom = j0 == 0 && !per_y;
+  template <bool INT> __device__ __forceinline__ void run_t(int j0, int jend) {
+    const bool ghost_bottom = !INT && j0 == 0 && !per_y;
     Fa = ghost_bottom ? 0 : j0 - 1;
-    const int Fb = stored(jend) ? jend : jend - 1;
+    const int Fb = (INT || stored(jend)) ? jend : jend - 1;
     nfetch = Fb - Fa + 1;
     nissued = 0;
     nwaited = 0;
     while (nissued < nfetch && nissued < P::NS) issue();
     Real P0[9], P1[9], P2[9], FS[9];
     uint32_t stj, stn = 0;
-    bool have_next;
+    bool have_next = false;
     if (ghost_bottom) {
       stj = wait();
-      stage_row(0, stj, P1);
+      stage_row<INT>(0, stj, P1);
       stn = wait();
-      stage_row(1, stn, P2);
+      stage_row<INT>(1, stn, P2);
       ghost_row(2, P1, P2, P0);
       have_next = true;
     } else {
-      stage_row(wrapr(j0 - 1), wait(), P0);
+      stage_row<INT>(INT ? j0 - 1 : wrapr(j0 - 1), wait(), P0);
       release(); // row j0-1 contributes phi only
       stj = wait();
-      stage_row(wrapr(j0), stj, P1);
-      have_next = false;
+      stage_row<INT>(INT ? j0 : wrapr(j0), stj, P1);
     }
-    if constexpr (!FD) yface(j0, P0, P1, FS);
-    // rows, unrolled by three so that the phi registers rotate without copies
-    int j = j0;
-    while (true) {
-      if (j >= jend) break;
-      row(j, jend, have_next, P0, P1, P2, FS, stj, stn);
-      have_next = false;
-      if (++j >= jend) break;
-      row(j, jend, false, P1, P2, P0, FS, stj, stn);
-      if (++j >= jend) break;
-      row(j, jend, false, P2, P0, P1, FS, stj, stn);
-      ++j;
+    if constexpr (!FD) yface<INT>(j0, P0, P1, FS);
+    // rows; the three phi rows rotate through register copies (a rolled loop
+    // keeps the instruction footprint small)
+    for (int j = j0; j < jend; ++j) {
+      row<INT>(j, jend, have_next, P0, P1, P2, FS, stj, stn);
+      if (!INT) have_next = false;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        P0[a] = P1[a];
+        P1[a] = P2[a];
+      }
     }
+  }
+
+  __device__ __forceinline__ void run(int sx, int sy) {
+    setup(sx);
+    const int j0 = sy * A.H;
+    const int jend = min(j0 + A.H, ny);
+    // inner strip: its 32 columns and the rows j0-1 .. jend all exist
+    const bool inner = i0 >= 1 && i0 + kStripCols <= nx - 1 && j0 >= 1 && jend <= ny - 1;
+    if (inner)
+      run_t<true>(j0, jend);
+    else
+      run_t<false>(j0, jend);
   }
 
   // After a timed-out wait: give the copies still in flight a bounded time
