@@ -206,6 +206,30 @@ DVBE_API dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pit
 /* Kernel launches issued since creation (every step kernel, init, reduction). */
 DVBE_API dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
 
+/* Allocation-free variant of dvbe_conserved.  The paper has no counterpart:
+ * this is an interface for callers that cannot allocate device memory, such as
+ * a framework that reserves all GPU memory for its own pool before the run, or
+ * a time-critical loop in which cudaMalloc / cudaFree must not run (cudaFree
+ * waits for the whole device).  It allocates nothing: the caller passes
+ * device pointers to f_tilde (storage `precision`, layout [9][ny][pitch] with
+ * element offsets, as dvbe_device_state reports it), to the cell widths
+ * dx[nx] and dy[ny], and to out[3], which receives sum rho |V|, sum rho u_x |V|
+ * and sum rho u_y |V| in FP64.  RT, rho0 and dev_scale are those of the
+ * solver that produced f_tilde.  Work is queued on `stream` (a cudaStream_t,
+ * NULL for the legacy default stream) and the call returns without waiting.
+ * Partial sums go to one fixed device array of 8192 x 3 doubles (192 KB) that
+ * every GPU loading the library keeps until exit; meshes of more than
+ * 33,554,432 cells (8192 x 4096) are rejected with DVBE_ERR_INVALID_ARG.
+ * Every call on a device shares that array and overwrites the slots it uses
+ * before reading them (nothing needs clearing), so calls that overlap on the
+ * GPU race.  The first call on each device resolves the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture. */
+DVBE_API dvbe_status dvbe_conserved_noalloc(const void *f_tilde, int precision, int nx, int ny,
+                                            long long pitch, const double *dx, const double *dy,
+                                            double RT, double rho0, double dev_scale, double *out,
+                                            void *stream);
+
 /* ---- batched form --------------------------------------------------------- */
 
 /* Many independent cases of uneven size stepped together: every step is one

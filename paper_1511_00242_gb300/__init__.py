@@ -107,6 +107,9 @@ _SIGS = {
     "dvbe_batch_set_launch": [ctypes.c_void_p, ctypes.POINTER(dvbe_launch)],
     "dvbe_batch_autotune": [ctypes.c_void_p, ctypes.c_int, _DP],
     "dvbe_batch_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "dvbe_conserved_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p],
     "dvbe_last_error": [],
     "dvbe_version": [],
 }
@@ -240,6 +243,17 @@ def make_params(case: dict, mesh, precision="f64", stream=None, allow_cfl_ge_1=F
     p.dev_scale = float(dev_scale)
     p.cuda_stream = stream if stream is None else ctypes.c_void_p(int(stream))
     return p, keep
+
+
+def dvbe_conserved_noalloc(f_tilde_ptr, precision, nx, ny, pitch, dx_ptr, dy_ptr, RT, rho0,
+                           dev_scale, out_ptr, stream=None):
+    """Allocation-free FP64 mass / momentum sums over caller-owned device
+    buffers (all pointers are device addresses as ints); see include/dvbe.h."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _call("dvbe_conserved_noalloc", ctypes.c_void_p(f_tilde_ptr), prec, int(nx), int(ny),
+          int(pitch), ctypes.c_void_p(dx_ptr), ctypes.c_void_p(dy_ptr), float(RT), float(rho0),
+          float(dev_scale), ctypes.c_void_p(out_ptr),
+          None if stream is None else ctypes.c_void_p(int(stream)))
 
 
 def dvbe_solver_create(params):
