@@ -45,12 +45,31 @@ def args_():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--launch", default=None,
+                   help="strip_rows,warps_per_block,blocks for the headline solver (skips its autotune)")
     return p.parse_args()
 
 
 def workload(n, scheme):
     case, fields = W.taylor_green_box(n, u0=0.01, cfl=0.5, scheme=scheme, dt_over_tau=10.0)
     return case, fields
+
+
+def measured_traffic(scheme, precision, cells):
+    """DRAM bytes per launch of the headline kernel from the committed ncu
+    capture (profiles/traffic.json), scaled to this mesh; None if the capture
+    is of another kernel or the kernel source has changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if t["kernel"] != f"k_step<{scheme}, {precision}>" or not sha.startswith(t["sha256_prefix"]):
+        return None
+    return t["dram_bytes_per_cell"] * cells
 
 
 def peaks():
@@ -185,7 +204,10 @@ def main():
     s = dv.Solver(case, precision=a.precision, stream=stream.cuda_stream)
     s.init_equilibrium(*fields)
     tuned_ms = None
-    if not a.no_autotune:
+    if a.launch:
+        h, w, b = (int(x) for x in a.launch.split(","))
+        s.set_launch(strip_rows=h, warps_per_block=w, blocks=b)
+    elif not a.no_autotune:
         tuned_ms = s.autotune(3)
     launch = s.get_launch()
     s.step(a.warmup)
@@ -263,7 +285,8 @@ def main():
                        "parallelism": f"replicas x{world}", "launch": launch,
                        "autotune_ms_per_step": tuned_ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": measured_traffic(a.scheme, a.precision, cells),
                          "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL[a.precision],
                          "kernel": f"k_step<{a.scheme}, {a.precision}>"},
