@@ -39,12 +39,15 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL")
+
+
 def _flags():
-    """NVCC flags; DVBE_MIN_BLOCKS (environment) sets the step kernel's
-    occupancy target, i.e. its register cap (1 -> up to 255 registers,
-    2 -> 128)."""
-    mb = os.environ.get("DVBE_MIN_BLOCKS", "1")
-    return NVCC_FLAGS + ["-DDVBE_MIN_BLOCKS=%d" % int(mb)]
+    """NVCC flags.  The step kernel's tuning knobs (occupancy target and
+    row-loop unrolling per scheme, defaults in step_kernel.cuh) may be
+    overridden by environment variables of the same names."""
+    extra = ["-D%s=%d" % (k, int(os.environ[k])) for k in KNOBS if k in os.environ]
+    return NVCC_FLAGS + extra
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:

@@ -31,8 +31,23 @@
 #include "internal.h"
 
 // Blocks of 256 threads the step kernel must fit per SM; sets its register cap.
-#ifndef DVBE_MIN_BLOCKS
-#define DVBE_MIN_BLOCKS 1
+// Occupancy target of the step kernel per scheme: blocks of 256 threads per
+// SM, which caps its registers (1: up to 255, 2: 128).  Measured on the
+// 4096^2 Taylor-Green step: DUGKS is fastest at 2 with a rolled row loop,
+// BKG at 1 with the row loop unrolled by three.
+#ifndef DVBE_DUGKS_MINB
+#define DVBE_DUGKS_MINB 2
+#endif
+#ifndef DVBE_BKG_MINB
+#define DVBE_BKG_MINB 1
+#endif
+// Inner-strip row loop of each scheme: 1 = unrolled by three (phi rows rotate
+// by renaming), 0 = rolled with register copies.
+#ifndef DVBE_DUGKS_UNROLL
+#define DVBE_DUGKS_UNROLL 0
+#endif
+#ifndef DVBE_BKG_UNROLL
+#define DVBE_BKG_UNROLL 1
 #endif
 
 namespace dvbe {
@@ -230,13 +245,19 @@ __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Re
 // DUGKS: face moments of f_bar, f_eq there and f = p f_bar + q f_eq for the
 // directions crossing the face (AXIS 0: x-face, e_x != 0; 1: y-face).
 template <typename Real, int AXIS>
-__device__ __forceinline__ void dugks_face(Real (&fb)[9], Real rho0, Real p, Real q) {
+__device__ __forceinline__ void dugks_face(Real (&fb)[9], Real rho0, Real p, Real qw1, Real qw2) {
   Real rp, rho, Ux, Uy;
   moments(fb, rho0, rp, rho, Ux, Uy);
-  Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
+  const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
+  // q f_eq - q w rref = q w (rho' + rho P), q w folded per weight class
+  const Real qr1 = qw1 * rho, qp1 = qw1 * rp, qr2 = qw2 * rho, qp2 = qw2 * rp;
 #pragma unroll
   for (int a = 1; a < 9; ++a) {
-    if ((AXIS == 0 ? EX(a) : EY(a)) != 0) fb[a] = p * fb[a] + q * deq_of<Real>(a, rp, rho, Ux, Uy, u15);
+    if ((AXIS == 0 ? EX(a) : EY(a)) != 0) {
+      const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
+      const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
+      fb[a] = p * fb[a] + (a <= 4 ? qr1 * Pq + qp1 : qr2 * Pq + qp2);
+    }
   }
 }
 
@@ -367,7 +388,7 @@ template <int SCHEME, int ST> struct Strip {
   K<Real> k;
   int lane, i, nx, ny, i0, xs, xwrapW;
   bool valid, per_x, per_y, touchW, touchE, out_lane, wrapW, wrapE;
-  Real a_phi, b_phi, p_face, q_face;
+  Real a_phi, b_phi, p_face, qw1, qw2; // qw1/2 = q times the axis / diagonal weight
   // x-face coefficients of this lane: right part of its west face, left part
   // of its east face; tangential / update factors of its column.
   Real cR[3], cL[3], tR0, tL0, txc, cxu;
@@ -467,7 +488,8 @@ template <int SCHEME, int ST> struct Strip {
     a_phi = Real(A.a_phi);
     b_phi = Real(A.b_phi);
     p_face = Real(A.p_face);
-    q_face = Real(A.q_face);
+    qw1 = Real(A.q_face * WGT(1));
+    qw2 = Real(A.q_face * WGT(5));
     if constexpr (FD) {
       Real nux = Real(A.fd_nux), nuy = Real(A.fd_nuy);
       kx1 = Real(0.5) * nux;
@@ -590,9 +612,8 @@ template <int SCHEME, int ST> struct Strip {
 
   // Flux values of the x-face west of this lane's cell at row j.
   template <bool INT>
-  __device__ __forceinline__ void xface(int j, const Real (&Pm)[9], const Real (&P0)[9],
+  __device__ __forceinline__ void xface(int j, Real tyc, const Real (&Pm)[9], const Real (&P0)[9],
                                         const Real (&Pp)[9], Real (&F)[9]) {
-    const Real tyc = ((const Real *)A.yct)[j + 1];
     const Real tL = tyc * tL0, tR = tyc * tR0;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -613,15 +634,14 @@ template <int SCHEME, int ST> struct Strip {
         face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
       }
     }
-    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, p_face, q_face);
+    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, p_face, qw1, qw2);
   }
 
   // Flux values of the y-face kf (between rows kf-1 and kf) at this column;
   // Pl = phi of row kf-1, Pu = phi of row kf.
   template <bool INT>
-  __device__ __forceinline__ void yface(int kf, const Real (&Pl)[9], const Real (&Pu)[9],
-                                        Real (&F)[9]) {
-    const Real th = ((const Real *)A.yfth)[kf + 1], s = ((const Real *)A.yfs)[kf + 1];
+  __device__ __forceinline__ void yface(int kf, Real th, Real s, const Real (&Pl)[9],
+                                        const Real (&Pu)[9], Real (&F)[9]) {
     const Real a0 = Real(1) - th, b0 = th;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -645,7 +665,7 @@ template <int SCHEME, int ST> struct Strip {
       const int side = kf == 0 ? 2 : 3;
       face_bc<Real>(A.seg[side][side == 2 ? segS : segN], 0, side == 2 ? -1 : 1, k.rho0, F);
     }
-    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, p_face, q_face);
+    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, p_face, qw1, qw2);
   }
 
   __device__ __forceinline__ void store_row(int j, const Real (&v)[9]) {
@@ -663,10 +683,9 @@ template <int SCHEME, int ST> struct Strip {
   // recomputed from the staged deviations d and phi = f_bar^+ as
   // f_tilde^+ = (4 phi - d) / 3 (the two transforms of Sec 2.2 combined).
   template <bool INT>
-  __device__ __forceinline__ void update_fv(int j, uint32_t stage, const Real (&Pb)[9],
+  __device__ __forceinline__ void update_fv(int j, Real cyu, uint32_t stage, const Real (&Pb)[9],
                                             const Real (&FW)[9], const Real (&FS)[9],
                                             const Real (&FN)[9]) {
-    const Real cyu = ((const Real *)A.ycu)[j + 1];
     Real v[9];
     if constexpr (DUG) {
       Real d[9];
@@ -724,15 +743,35 @@ template <int SCHEME, int ST> struct Strip {
   __device__ __forceinline__ bool stored(int L) const { return per_y || (L >= 0 && L < ny); }
   __device__ __forceinline__ int wrapr(int L) const { return L < 0 ? L + ny : (L >= ny ? L - ny : L); }
 
+  // Per-row mesh factors of rows jb .. jb+31, one row per lane, broadcast by
+  // shuffles: tangential factor and update factor of row j, theta and slope
+  // factor of the y-face j+1.
+  struct RowTab {
+    Real tyc, cyu, th, s;
+    int jb;
+  };
+  __device__ __forceinline__ void load_rows(RowTab &t, int jb) {
+    const int j = min(jb + lane, ny - 1);
+    t.tyc = ((const Real *)A.yct)[j + 1];
+    t.cyu = ((const Real *)A.ycu)[j + 1];
+    t.th = ((const Real *)A.yfth)[j + 2];
+    t.s = ((const Real *)A.yfs)[j + 2];
+    t.jb = jb;
+  }
+
   // One full row j: phi of row j+1 into Pc (unless have_next), faces, update.
   // Pa, Pb, Pc = phi of rows j-1, j, j+1; stj / stn = stages holding rows j
   // and j+1 (stj is released at the end of the row).  INT: the strip touches
   // no boundary (all its columns and rows j0-1 .. jend are inner cells), so
   // the ghost, wrap and boundary-face code is compiled out.
   template <bool INT>
-  __device__ __forceinline__ void row(int j, int jend, bool have_next, Real (&Pa)[9],
+  __device__ __forceinline__ void row(int j, int jend, bool have_next, RowTab &rt, Real (&Pa)[9],
                                       Real (&Pb)[9], Real (&Pc)[9], Real (&FS)[9], uint32_t &stj,
                                       uint32_t &stn) {
+    if (j - rt.jb >= 32) load_rows(rt, j);
+    const int q = j - rt.jb;
+    const Real tyc = __shfl_sync(kFull, rt.tyc, q), cyu = __shfl_sync(kFull, rt.cyu, q);
+    const Real th = __shfl_sync(kFull, rt.th, q), sl = __shfl_sync(kFull, rt.s, q);
     if (INT || !have_next) {
       if (INT || stored(j + 1)) {
         stn = wait();
@@ -746,9 +785,9 @@ template <int SCHEME, int ST> struct Strip {
       update_fd(j, Pa, Pb, Pc);
     } else {
       Real FW[9], FN[9];
-      xface<INT>(j, Pa, Pb, Pc, FW);
-      yface<INT>(j + 1, Pb, Pc, FN);
-      update_fv<INT>(j, stj, Pb, FW, FS, FN);
+      xface<INT>(j, tyc, Pa, Pb, Pc, FW);
+      yface<INT>(j + 1, th, sl, Pb, Pc, FN);
+      update_fv<INT>(j, cyu, stj, Pb, FW, FS, FN);
 #pragma unroll
       for (int a = 0; a < 9; ++a) FS[a] = FN[a];
     }
@@ -764,6 +803,8 @@ template <int SCHEME, int ST> struct Strip {
     nissued = 0;
     nwaited = 0;
     while (nissued < nfetch && nissued < P::NS) issue();
+    RowTab rt;
+    load_rows(rt, j0);
     Real P0[9], P1[9], P2[9], FS[9];
     uint32_t stj, stn = 0;
     bool have_next = false;
@@ -780,16 +821,30 @@ template <int SCHEME, int ST> struct Strip {
       stj = wait();
       stage_row<INT>(INT ? j0 : wrapr(j0), stj, P1);
     }
-    if constexpr (!FD) yface<INT>(j0, P0, P1, FS);
-    // rows; the three phi rows rotate through register copies (a rolled loop
-    // keeps the instruction footprint small)
-    for (int j = j0; j < jend; ++j) {
-      row<INT>(j, jend, have_next, P0, P1, P2, FS, stj, stn);
-      if (!INT) have_next = false;
+    if constexpr (!FD)
+      yface<INT>(j0, ((const Real *)A.yfth)[j0 + 1], ((const Real *)A.yfs)[j0 + 1], P0, P1, FS);
+    if constexpr (INT && (DUG ? DVBE_DUGKS_UNROLL : DVBE_BKG_UNROLL)) {
+      // unrolled by three so that the phi rows rotate by renaming
+      int j = j0;
+      while (true) {
+        if (j >= jend) break;
+        row<true>(j, jend, false, rt, P0, P1, P2, FS, stj, stn);
+        if (++j >= jend) break;
+        row<true>(j, jend, false, rt, P1, P2, P0, FS, stj, stn);
+        if (++j >= jend) break;
+        row<true>(j, jend, false, rt, P2, P0, P1, FS, stj, stn);
+        ++j;
+      }
+    } else {
+      // rolled loop with register copies: the boundary path stays small
+      for (int j = j0; j < jend; ++j) {
+        row<INT>(j, jend, have_next, rt, P0, P1, P2, FS, stj, stn);
+        have_next = false;
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        P0[a] = P1[a];
-        P1[a] = P2[a];
+        for (int a = 0; a < 9; ++a) {
+          P0[a] = P1[a];
+          P1[a] = P2[a];
+        }
       }
     }
   }
@@ -824,7 +879,8 @@ template <int SCHEME, int ST> struct Strip {
 };
 
 template <int SCHEME, int ST>
-__global__ void __launch_bounds__(256, DVBE_MIN_BLOCKS) k_step(const __grid_constant__ CaseArgs A) {
+__global__ void __launch_bounds__(256, SCHEME == SC_DUGKS ? DVBE_DUGKS_MINB : DVBE_BKG_MINB)
+    k_step(const __grid_constant__ CaseArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   using P = Pipe<(int)sizeof(typename StoreT<ST>::T)>;
   const int lane = threadIdx.x & 31;

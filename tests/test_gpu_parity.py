@@ -306,3 +306,45 @@ def test_batch_divergent_case_is_isolated(dv):
             np.testing.assert_allclose(b.get_f(0), s.get_f(), rtol=0, atol=0)
     finally:
         b.close()
+
+
+# ------------------------------------------------------------------ degenerate cases
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_collisionless_limit(dv, scheme):
+    """tau -> infinity (Omega -> 0): pure Lax-Wendroff advection."""
+    case = periodic_case(40, 33, scheme, tau=1e30)
+    g, o = run_pair(dv, case, 50, seed=12, amp_neq=1e-2)
+    assert rel_err(g, o) < TOL64
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_large_dt_over_tau(dv, scheme):
+    """dt/tau = 100 (the paper's largest Taylor-Green ratio), FP64 parity."""
+    case = periodic_case(50, 41, scheme)
+    case["tau"] = case["dt"] / 100.0
+    g, o = run_pair(dv, case, 100, seed=13, amp_neq=1e-4)
+    assert rel_err(g, o) < TOL64
+
+
+def test_zero_steps_and_counts(dv):
+    case, fields = W.taylor_green_box(32)
+    with dv.Solver(case) as s:
+        s.init_equilibrium(*fields)
+        f0 = s.get_f()
+        l0 = s.launch_count()
+        s.step(0)
+        assert s.launch_count() == l0 and s.step_count() == 0
+        np.testing.assert_array_equal(s.get_f(), f0)
+
+
+def test_cfl_above_one_blows_up(dv):
+    """With the CFL check overridden (CFL 1.6), the scheme is unstable, as
+    the paper reports for CFL > 1; the divergence flag reports it."""
+    case, fields = W.taylor_green_box(64, u0=0.05, cfl=1.6)
+    with dv.Solver(case, precision="f32", allow_cfl_ge_1=True) as s:
+        s.init_equilibrium(*fields)
+        with pytest.raises(dv.DvbeError) as e:
+            for _ in range(200):
+                s.step(50)
+        assert e.value.status == dv.DVBE_ERR_DIVERGED
