@@ -295,6 +295,23 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const void *tmap, int x,
       "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
+// The row copy of one stage, issued by the lanes with on != 0 (lane 0),
+// without a branch: expect_tx on the stage's mbarrier, then the tensor copy.
+__device__ __forceinline__ void tma_row_pred(uint32_t on, uint32_t bar, uint32_t bytes, uint32_t dst,
+                                             const void *tmap, int x, int y) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.u32 p, %0, 0;\n"
+      "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n"
+      "@p cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%3], [%4, {%5, %6, %7}], [%1]; }" ::"r"(on),
+      "r"(bar), "r"(bytes), "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(0)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_pred(uint32_t on) {
+  asm volatile("{ .reg .pred p; setp.ne.u32 p, %0, 0; @p fence.proxy.async.shared::cta; }" ::"r"(on)
+               : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -401,23 +418,28 @@ template <int SCHEME, int ST> struct Strip {
   uint32_t sbase, bbase, txbytes;
   uint32_t lds_off; // byte offset of this lane's first value inside a stage
   bool wrap_lane;   // reads a periodic wrap copy (fields 16 bytes apart)
-  // Fetches are issued and waited for in order; islot / cslot are the stages
-  // of the next issue / wait and cphase holds the parity to wait for on each
-  // stage.  These persist across the strips a warp processes.
+  // Fetches are issued and waited for in order through the NS stages, so
+  // every stage in one pass of the ring completes a phase of the same parity:
+  // islot / cslot are the stages of the next issue / wait and cpar the parity
+  // of the current pass.  These persist across the strips a warp processes.
   int islot, cslot;
-  uint32_t cphase;
+  uint32_t cpar;
   int nfetch, nissued, nwaited; // of the current strip
   int Fa;                       // logical row of fetch 0
   bool timeout;
+  int tslot;     // stage of the wait that ran out
+  uint32_t tpar; // and its parity
 
   __device__ __forceinline__ Strip(const CaseArgs &args, int lane_, uint32_t sbase_)
       : A(args), lane(lane_), sbase(sbase_) {
     bbase = sbase + P::NS * P::STAGEB;
     islot = 0;
     cslot = 0;
-    cphase = 0;
+    cpar = 0;
     bad = false;
     timeout = false;
+    tslot = 0;
+    tpar = 0;
   }
 
   __device__ __forceinline__ void init_barriers() {
@@ -502,46 +524,49 @@ template <int SCHEME, int ST> struct Strip {
   }
 
   // ---- row pipeline: fetch number q of this strip is logical row Fa + q
-  __device__ __forceinline__ void issue() {
-    if (lane == 0 && !timeout) {
-      const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
-      const int r = wrapr(Fa + nissued);
-      mbar_expect_tx(bar, txbytes);
-      tma_load3(dst, &A.tm_main, xs, r, 0, bar);
-      if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, xwrapW, r, 0, bar);
-      if (wrapE) tma_load3(dst + P::MAINB + P::WRAPB, &A.tm_wrap, 0, r, 0, bar);
+  template <bool INT> __device__ __forceinline__ void issue() {
+    const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
+    const int r = INT ? Fa + nissued : wrapr(Fa + nissued);
+    tma_row_pred((uint32_t)(lane == 0 && !timeout), bar, txbytes, dst, &A.tm_main, xs, r);
+    if (!INT && (wrapW || wrapE)) {
+      if (lane == 0 && !timeout) {
+        if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, xwrapW, r, 0, bar);
+        if (wrapE) tma_load3(dst + P::MAINB + P::WRAPB, &A.tm_wrap, 0, r, 0, bar);
+      }
     }
     islot = islot + 1 == P::NS ? 0 : islot + 1;
     ++nissued;
   }
 
-  // Wait (bounded) for the next fetch in order; returns its stage address.
-  // A lane whose wait runs out stops waiting from then on; the warp checks
-  // the flag once per strip.
+  // Bounded wait after a failed first poll; a lane whose wait runs out stops
+  // waiting from then on (the warp checks the flag once per strip).
+  __device__ __forceinline__ void wait_slow(uint32_t bar, uint32_t par) {
+    if (timeout) return;
+    for (uint32_t n = 0; n < kSpinLimit; ++n)
+      if (mbar_try_wait(bar, par)) return;
+    timeout = true;
+    tslot = cslot;
+    tpar = par;
+  }
+
+  // Wait for the next fetch in order; returns its stage address.
   __device__ __forceinline__ uint32_t wait() {
-    const uint32_t st = sbase + cslot * P::STAGEB;
-    if (!timeout) {
-      const uint32_t bar = bbase + 8 * cslot, par = (cphase >> cslot) & 1u;
-      uint32_t n = 0;
-      while (!mbar_try_wait(bar, par)) {
-        if (++n >= kSpinLimit) {
-          timeout = true;
-          break;
-        }
-      }
-      if (!timeout) ++nwaited;
+    const uint32_t st = sbase + cslot * P::STAGEB, bar = bbase + 8 * cslot;
+    if (!mbar_try_wait(bar, cpar)) wait_slow(bar, cpar);
+    ++nwaited;
+    if (++cslot == P::NS) {
+      cslot = 0;
+      cpar ^= 1u;
     }
-    cphase ^= 1u << cslot;
-    cslot = cslot + 1 == P::NS ? 0 : cslot + 1;
     return st;
   }
 
   // The oldest held stage is no longer read: reuse it for the next fetch.
-  __device__ __forceinline__ void release() {
+  template <bool INT> __device__ __forceinline__ void release() {
     if (nissued < nfetch) {
       __syncwarp();
-      if (lane == 0) fence_proxy_async();
-      issue();
+      fence_proxy_async_pred((uint32_t)(lane == 0));
+      issue<INT>();
     }
   }
 
@@ -776,7 +801,7 @@ template <int SCHEME, int ST> struct Strip {
       if (INT || stored(j + 1)) {
         stn = wait();
         stage_row<INT>(INT ? j + 1 : wrapr(j + 1), stn, Pc);
-        if (j + 1 == jend) release(); // only phi of this row is needed
+        if (j + 1 == jend) release<INT>(); // only phi of this row is needed
       } else {
         ghost_row(3, Pb, Pa, Pc);
       }
@@ -791,7 +816,7 @@ template <int SCHEME, int ST> struct Strip {
 #pragma unroll
       for (int a = 0; a < 9; ++a) FS[a] = FN[a];
     }
-    release();
+    release<INT>();
     stj = stn;
   }
 
@@ -802,7 +827,7 @@ template <int SCHEME, int ST> struct Strip {
     nfetch = Fb - Fa + 1;
     nissued = 0;
     nwaited = 0;
-    while (nissued < nfetch && nissued < P::NS) issue();
+    while (nissued < nfetch && nissued < P::NS) issue<INT>();
     RowTab rt;
     load_rows(rt, j0);
     Real P0[9], P1[9], P2[9], FS[9];
@@ -817,7 +842,7 @@ template <int SCHEME, int ST> struct Strip {
       have_next = true;
     } else {
       stage_row<INT>(INT ? j0 - 1 : wrapr(j0 - 1), wait(), P0);
-      release(); // row j0-1 contributes phi only
+      release<INT>(); // row j0-1 contributes phi only
       stj = wait();
       stage_row<INT>(INT ? j0 : wrapr(j0), stj, P1);
     }
@@ -863,17 +888,21 @@ template <int SCHEME, int ST> struct Strip {
 
   // After a timed-out wait: give the copies still in flight a bounded time
   // to land before the warp leaves (their shared memory must stay valid).
-  // Fetches nwaited .. nissued-1 are outstanding; the first of them was due
-  // on the stage before cslot.
+  // The fetch that timed out was on stage tslot with parity tpar; it and the
+  // later issued ones are outstanding.
   __device__ __forceinline__ void drain() {
-    int s = cslot - 1 < 0 ? P::NS - 1 : cslot - 1;
-    uint32_t ph = cphase ^ (1u << s); // undo the flip of the timed-out wait
-    for (int q = nwaited; q < nissued; ++q) {
+    if (!timeout) return;
+    int s = tslot;
+    uint32_t par = tpar;
+    const int waited_ok = nwaited - 1; // the timed-out wait was counted
+    for (int q = waited_ok; q < nissued; ++q) {
       uint32_t n = 0;
-      while (!mbar_try_wait(bbase + 8 * s, (ph >> s) & 1u) && ++n < (1u << 16)) {
+      while (!mbar_try_wait(bbase + 8 * s, par) && ++n < (1u << 16)) {
       }
-      ph ^= 1u << s;
-      s = s + 1 == P::NS ? 0 : s + 1;
+      if (++s == P::NS) {
+        s = 0;
+        par ^= 1u;
+      }
     }
   }
 };
@@ -941,10 +970,10 @@ __global__ void __launch_bounds__(256, 1)
     Strip<SCHEME, ST> s(A, lane, sb);
     s.islot = pipe_slot;
     s.cslot = pipe_slot;
-    s.cphase = pipe_phase;
+    s.cpar = pipe_phase;
     s.run((int)(local % A.strips_x), (int)(local / A.strips_x));
     pipe_slot = s.cslot;
-    pipe_phase = s.cphase;
+    pipe_phase = s.cpar;
     if (__any_sync(kFull, s.bad) && lane == 0) atomicOr(A.flag, 1u);
     if (__any_sync(kFull, s.timeout)) {
       s.drain();
