@@ -34,7 +34,9 @@
  *   - Diffuse wall (parity unpinned apart from zero normal mass flux): the
  *     incoming values are f_eq(rho_w, U_w) with rho_w making the normal mass
  *     flux through the face zero.
- *   - Inflow: ghosts and all face values are f_eq(rho_inf, U_inf); outflow:
+ *   - Free stream / inflow (Sec 3.3): ghosts are f_eq(rho_inf, U_inf) and,
+ *     at the boundary face, the distributions entering the domain are set
+ *     to it (those leaving keep their reconstructed values); outflow:
  *     zero-gradient ghosts; symmetry: mirrored ghosts.
  */
 #include "dvbe_oracle.h"
@@ -459,9 +461,17 @@ static void face_bc(const vset *v, const orc_bc_segment *s, double nxo, double n
       }
       break;
     }
-    case ORC_BC_INFLOW_EQ:
-      feq_of(v, s->rho, s->ux, s->uy, val);
+    case ORC_BC_INFLOW_EQ: {
+      /* free stream: what enters the domain is the free-stream equilibrium;
+         what leaves keeps its reconstructed value */
+      double fe[9];
+      feq_of(v, s->rho, s->ux, s->uy, fe);
+      for (int a = 0; a < 9; ++a) {
+        double xn = v->xi[a][0] * nxo + v->xi[a][1] * nyo;
+        if (xn < 0.0) val[a] = fe[a];
+      }
       break;
+    }
     default:
       break;
   }
