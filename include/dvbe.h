@@ -49,9 +49,12 @@ typedef enum {
 typedef enum { DVBE_DUGKS = 0, DVBE_BKG = 1 } dvbe_scheme;
 
 /* Storage of f_tilde in device memory.  Arithmetic is FP64 for DVBE_F64 and
- * FP32 for every other mode; all modes compute on deviations
- * f_tilde - w_alpha rho0.  *_DEV modes store d = (f_tilde - w_alpha rho0)/s_alpha
- * with the per-field scale s_alpha = dev_scale * w_alpha * rho0. */
+ * FP32 for every other mode.  *_DEV modes store d = (f_tilde - w_alpha rho0)/s_alpha;
+ * s_alpha = 1 for DVBE_F32_DEV and, for the 16-bit modes, the power of two
+ * nearest to dev_scale * w_alpha * rho0 (exact to apply and undo).  The FP32
+ * modes, DVBE_F32 included, compute on deviations of f_tilde from a fixed
+ * reference near w_alpha rho0, so rounding scales with the deviation;
+ * DVBE_F32 still stores f_tilde itself, rounded to FP32 every step. */
 typedef enum {
   DVBE_F64 = 0,
   DVBE_F32 = 1,
@@ -65,7 +68,8 @@ typedef enum {
   DVBE_BC_PERIODIC = 0,        /* must pair W with E or S with N, one segment   */
   DVBE_BC_WALL_BOUNCEBACK = 1, /* ghost extrapolation + half-way bounce-back    */
   DVBE_BC_WALL_DIFFUSE = 2,    /* ghost extrapolation + diffuse reflection      */
-  DVBE_BC_INFLOW_EQ = 3,       /* ghosts and face values f_eq(rho, ux, uy)      */
+  DVBE_BC_INFLOW_EQ = 3,       /* free stream: ghosts f_eq(rho, ux, uy); at the
+                                  face the entering distributions take it      */
   DVBE_BC_OUTFLOW_ZG = 4,      /* zero-gradient ghosts                          */
   DVBE_BC_SYMMETRY = 5         /* mirrored ghosts                               */
 } dvbe_bc_kind;
@@ -98,8 +102,9 @@ typedef struct {
   int allow_cfl_ge_1; /* non-zero: accept CFL >= 1 (the paper's blow-up test)    */
   int bkg_fd;       /* BKG on a uniform mesh: use the finite-difference form of
                        Eqs. bkgfd / central_schemes (identical up to rounding)   */
-  double dev_scale; /* s_alpha = dev_scale w_alpha rho0 for *_DEV (0 -> default:
-                       1/256 for F16, 1 otherwise)                               */
+  double dev_scale; /* s_alpha = power of two nearest dev_scale w_alpha rho0 for
+                       F16_DEV / BF16_DEV (0 -> default: 1/256 for F16, 1 for
+                       BF16); ignored otherwise (F32_DEV stores d unscaled)     */
   void *cuda_stream; /* cudaStream_t to run on (NULL: the library creates its own
                         non-blocking stream)                                    */
 } dvbe_params;

@@ -23,27 +23,28 @@ __host__ __device__ constexpr double AW(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
+__host__ __device__ constexpr int AWC(int a) { return a == 0 ? 0 : (a <= 4 ? 1 : 2); }
+
 // Read / write f_tilde_alpha of one cell in any storage mode, in FP64.
 __device__ __forceinline__ double rd(const FieldView &v, int a, long long idx) {
-  const double base = AW(a) * v.rho0;
+  const double base = AW(a) * v.rho0, sc = v.scale[AWC(a)];
   switch (v.store) {
     case ST_F64:
       return ((const double *)v.f)[a * v.plane + idx];
     case ST_F32:
       return (double)((const float *)v.f)[a * v.plane + idx];
     case ST_F32_DEV:
-      return base + v.sigma * base * (double)((const float *)v.f)[a * v.plane + idx];
+      return base + sc * (double)((const float *)v.f)[a * v.plane + idx];
     case ST_F16_DEV:
-      return base + v.sigma * base * (double)__half2float(((const __half *)v.f)[a * v.plane + idx]);
+      return base + sc * (double)__half2float(((const __half *)v.f)[a * v.plane + idx]);
     default:
-      return base + v.sigma * base *
-                        (double)__bfloat162float(((const __nv_bfloat16 *)v.f)[a * v.plane + idx]);
+      return base + sc * (double)__bfloat162float(((const __nv_bfloat16 *)v.f)[a * v.plane + idx]);
   }
 }
 
 __device__ __forceinline__ void wr(const FieldView &v, int a, long long idx, double x) {
   const double base = AW(a) * v.rho0;
-  const double d = (x - base) / (v.sigma * base);
+  const double d = (x - base) / v.scale[AWC(a)];
   switch (v.store) {
     case ST_F64:
       ((double *)v.f)[a * v.plane + idx] = x;

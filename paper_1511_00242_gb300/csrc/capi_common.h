@@ -17,7 +17,8 @@ namespace dvbe {
 struct Problem {
   int nx = 0, ny = 0;
   std::vector<double> xf, yf;
-  double RT = 0, tau = 0, dt = 0, rho0 = 1, sigma = 1, c = 1, cfl = 0;
+  double RT = 0, tau = 0, dt = 0, rho0 = 1, c = 1, cfl = 0;
+  double scale[3] = {1, 1, 1}; // deviation storage scale per weight class
   int user_scheme = 0, kernel = 0, store = 0;
   bool per_x = false, per_y = false;
   std::vector<dvbe_bc_segment> bc[4];

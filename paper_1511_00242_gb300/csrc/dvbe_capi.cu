@@ -83,6 +83,16 @@ cudaError_t launch_step_batch(int store, int scheme, const CaseArgs *c, const lo
 // problem set-up shared by the solver and the batch
 // ---------------------------------------------------------------------------
 
+void deviation_scales(int precision, double dev_scale, double rho0, double out[3]) {
+  if (precision != DVBE_F16_DEV && precision != DVBE_BF16_DEV) {
+    out[0] = out[1] = out[2] = 1.0;
+    return;
+  }
+  const double sigma = dev_scale > 0 ? dev_scale : (precision == DVBE_F16_DEV ? 1.0 / 256.0 : 1.0);
+  const double w[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+  for (int c = 0; c < 3; ++c) out[c] = std::exp2(std::floor(std::log2(sigma * w[c] * rho0) + 0.5));
+}
+
 static int elem_bytes(int store) {
   return store == ST_F64 ? 8 : ((store == ST_F16_DEV || store == ST_BF16_DEV) ? 2 : 4);
 }
@@ -122,7 +132,7 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   pb.rho0 = p->rho0 > 0 ? p->rho0 : 1.0;
   pb.user_scheme = p->scheme;
   pb.store = p->precision;
-  pb.sigma = p->dev_scale > 0 ? p->dev_scale : (p->precision == DVBE_F16_DEV ? 1.0 / 256.0 : 1.0);
+  deviation_scales(p->precision, p->dev_scale, pb.rho0, pb.scale);
   bool per[4];
   for (int s = 0; s < 4; ++s) {
     if (p->nbc[s] < 1 || p->nbc[s] > DVBE_MAX_SEGMENTS || !p->bc[s])
@@ -326,7 +336,7 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   a.b_tp = pb.b_tp;
   a.p_face = pb.p_face;
   a.q_face = pb.q_face;
-  a.dev_sigma = pb.sigma;
+  for (int c = 0; c < 3; ++c) a.dev_scale[c] = pb.scale[c];
   a.fd_nux = pb.fd_nux;
   a.fd_nuy = pb.fd_nuy;
   a.xfth = dp.blob + off[0];
@@ -366,7 +376,7 @@ FieldView view_of(const Problem &pb, void *f) {
   v.ny = pb.ny;
   v.store = pb.store;
   v.rho0 = pb.rho0;
-  v.sigma = pb.sigma;
+  for (int c = 0; c < 3; ++c) v.scale[c] = pb.scale[c];
   v.RT = pb.RT;
   v.tau = pb.tau;
   v.dt = pb.dt;

@@ -48,7 +48,7 @@ struct CaseArgs {
   double a_phi, b_phi;   // phi = a delta + b delta_eq   (DUGKS: f_bar^+, BKG: f_tilde^+)
   double a_tp, b_tp;     // f_tilde^+ = a delta + b delta_eq (DUGKS update)
   double p_face, q_face; // DUGKS face: f = p f_bar + q f_eq
-  double dev_sigma;      // deviation storage: s_alpha = dev_sigma w_alpha rho0
+  double dev_scale[3];   // deviation storage scale per weight class (rest, axis, diagonal)
   double fd_nux, fd_nuy; // BKG-FD: c dt / dx, c dt / dy (uniform meshes)
 
   // Geometry tables in compute precision (double for F64, float otherwise).
@@ -77,8 +77,15 @@ struct FieldView {
   void *f; // storage base
   long long plane;
   int pitch, nx, ny, store;
-  double rho0, sigma, RT, tau, dt;
+  double rho0, scale[3], RT, tau, dt; // scale: deviation storage scale per weight class
 };
+
+// Deviation-storage scales per weight class (rest, axis, diagonal).  16-bit
+// modes: the power of two nearest to dev_scale * w * rho0, so that scaling in
+// and out is exact; dev_scale <= 0 selects the default (1/256 for FP16, 1 for
+// BF16).  FP32 deviations are stored unscaled (a power-of-two scale changes
+// no FP32 rounding) and the other modes have no scale: 1.
+void deviation_scales(int precision, double dev_scale, double rho0, double out[3]);
 cudaError_t aux_init_eq(const FieldView &v, const double *d_rho, const double *d_ux,
                         const double *d_uy, cudaStream_t s);
 cudaError_t aux_init_ce(const FieldView &v, const double *d_rho, const double *d_ux,

@@ -51,23 +51,22 @@ struct View {
   const void *f;
   long long pitch, plane;
   int nx, ny, store;
-  double rho0, sigma, c;
+  double rho0, scale[3], c;
 };
 
 __device__ __forceinline__ double value(const View &v, int a, long long idx) {
-  const double base = NW(a) * v.rho0;
+  const double base = NW(a) * v.rho0, sc = v.scale[a == 0 ? 0 : (a <= 4 ? 1 : 2)];
   switch (v.store) {
     case DVBE_F64:
       return ((const double *)v.f)[a * v.plane + idx];
     case DVBE_F32:
       return (double)((const float *)v.f)[a * v.plane + idx];
     case DVBE_F32_DEV:
-      return base + v.sigma * base * (double)((const float *)v.f)[a * v.plane + idx];
+      return base + sc * (double)((const float *)v.f)[a * v.plane + idx];
     case DVBE_F16_DEV:
-      return base + v.sigma * base * (double)__half2float(((const __half *)v.f)[a * v.plane + idx]);
+      return base + sc * (double)__half2float(((const __half *)v.f)[a * v.plane + idx]);
     default:
-      return base + v.sigma * base *
-                        (double)__bfloat162float(((const __nv_bfloat16 *)v.f)[a * v.plane + idx]);
+      return base + sc * (double)__bfloat162float(((const __nv_bfloat16 *)v.f)[a * v.plane + idx]);
   }
 }
 
@@ -169,7 +168,7 @@ extern "C" DVBE_API dvbe_status dvbe_conserved_noalloc(const void *f_tilde, int 
   v.ny = ny;
   v.store = precision;
   v.rho0 = rho0 > 0 ? rho0 : 1.0;
-  v.sigma = dev_scale > 0 ? dev_scale : (precision == DVBE_F16_DEV ? 1.0 / 256.0 : 1.0);
+  dvbe::deviation_scales(precision, dev_scale, v.rho0, v.scale);
   v.c = sqrt(3.0 * RT);
   cudaStream_t s = (cudaStream_t)stream;
   k_noalloc_sums<<<(int)nblocks, kNoAllocThreads, 0, s>>>(v, dx, dy, scratch);

@@ -19,10 +19,11 @@
 //   6. DUGKS: face moments, f_eq at the face and the back-transform to f,
 //   7. update f_tilde^{n+1} = f_tilde^+ - dt/|V| sum (xi . n) A f_face
 //      (Eqs. eq_update, lwfv, bkg_fv) and store.
-// Every face is computed once.  All arithmetic is on deviations
-// delta = f_tilde - w_alpha rho0: transforms, reconstruction and the flux
-// difference are affine with weights summing to one, so the constant drops
-// out and rounding scales with the deviation, not with f_tilde itself.
+// Every face is computed once.  FP32 arithmetic is on deviations
+// delta = f_tilde - c_alpha from a fixed reference c_alpha near w_alpha rho0:
+// transforms, reconstruction and the flux difference are affine with weights
+// summing to one, so the constant drops out and rounding scales with the
+// deviation, not with f_tilde itself.  FP64 works on f_tilde directly.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -65,6 +66,40 @@ __host__ __device__ constexpr int EY(int a) {
 __host__ __device__ constexpr double WGT(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
+// Cell-stage equilibrium coefficients whose sums are exact in the compute
+// precision.  fl(4/9), fl(1/9) and fl(1/36) share one relative rounding error
+// (+7.5e-9 in FP32), so with them the collision would add mass and momentum
+// at that rate in every cell and step.  Instead
+//   mass:      W0 + 4 W1 + 4 W2 = 1 exactly: W2 = 1/36 rounded to a multiple
+//              of 2^-26 (FP32) or 2^-55 (FP64), W1 = 4 W2, W0 = 1 - 20 W2;
+//   momentum:  2 G1 + 4 G2 = 1 exactly: G2 = 1/12 rounded likewise,
+//              G1 = (1 - 4 G2) / 2;
+// all representable.  d_eq = W (rho' + rho Q) + G (e . m), with m = sum e d
+// and Q = 4.5 (e.U)^2 - 1.5 |U|^2, is Eq. equilibrium regrouped; its mass and
+// momentum equal rho' and m up to unbiased rounding of each term.  W and G
+// differ from 4/9, 1/9, 1/36, 1/3, 1/12 by less than 1e-7 relative, which
+// moves only non-conserved moments (c_s^2 and the third moments) that much.
+template <typename Real> struct EqCoef;
+template <> struct EqCoef<float> {
+  static constexpr float W2 = 1864135.0f / 67108864.0f;     // 2^26
+  static constexpr float W1 = 4.0f * W2;
+  static constexpr float W0 = 7456541.0f / 16777216.0f;     // 1 - 20 W2, 2^24
+  static constexpr float G2 = 5592405.0f / 67108864.0f;     // 2^26
+  static constexpr float G1 = 11184811.0f / 33554432.0f;    // (1 - 4 G2) / 2, 2^25
+};
+template <> struct EqCoef<double> {
+  static constexpr double W2 = 1000799917193444.0 / 36028797018963968.0; // 2^55
+  static constexpr double W1 = 4.0 * W2;
+  static constexpr double W0 = 4003199668773772.0 / 9007199254740992.0;  // 2^53
+  static constexpr double G2 = 3002399751580331.0 / 36028797018963968.0; // 2^55
+  static constexpr double G1 = 6004799503160661.0 / 18014398509481984.0; // 2^54
+};
+static_assert(EqCoef<float>::W0 + 4.0f * EqCoef<float>::W1 + 4.0f * EqCoef<float>::W2 == 1.0f, "");
+static_assert(2.0f * EqCoef<float>::G1 + 4.0f * EqCoef<float>::G2 == 1.0f, "");
+static_assert(EqCoef<double>::W0 + 4.0 * EqCoef<double>::W1 + 4.0 * EqCoef<double>::W2 == 1.0, "");
+static_assert(2.0 * EqCoef<double>::G1 + 4.0 * EqCoef<double>::G2 == 1.0, "");
+static_assert(EqCoef<float>::W0 == 1.0f - 20.0f * EqCoef<float>::W2, "");
+static_assert(EqCoef<double>::W0 == 1.0 - 20.0 * EqCoef<double>::W2, "");
 __host__ __device__ constexpr int OPP(int a) {
   return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
 }
@@ -78,30 +113,36 @@ __host__ __device__ constexpr int MIRY(int a) { // e_y -> -e_y
 // ---- storage --------------------------------------------------------------
 
 template <int ST> struct StoreT;
+// Codec between the stored value x and the value the arithmetic works on:
+//   CODEC_ABS     f_tilde itself (reference 0): d = x
+//   CODEC_OFFSET  absolute storage, deviation arithmetic: d = x - c, x = c + d
+//   CODEC_DEV     deviations stored unscaled: d = x
+//   CODEC_SCALED  scaled deviations: d = s x, x = d / s (s a power of two)
+enum { CODEC_ABS, CODEC_OFFSET, CODEC_DEV, CODEC_SCALED };
 template <> struct StoreT<ST_F64> {
   using T = double;
   using Real = double;
-  static constexpr bool DEV = false;
+  static constexpr int CODEC = CODEC_ABS;
 };
 template <> struct StoreT<ST_F32> {
   using T = float;
   using Real = float;
-  static constexpr bool DEV = false;
+  static constexpr int CODEC = CODEC_OFFSET;
 };
 template <> struct StoreT<ST_F32_DEV> {
   using T = float;
   using Real = float;
-  static constexpr bool DEV = true;
+  static constexpr int CODEC = CODEC_DEV;
 };
 template <> struct StoreT<ST_F16_DEV> {
   using T = __half;
   using Real = float;
-  static constexpr bool DEV = true;
+  static constexpr int CODEC = CODEC_SCALED;
 };
 template <> struct StoreT<ST_BF16_DEV> {
   using T = __nv_bfloat16;
   using Real = float;
-  static constexpr bool DEV = true;
+  static constexpr int CODEC = CODEC_SCALED;
 };
 
 __device__ __forceinline__ double to_real(double x) { return x; }
@@ -136,20 +177,30 @@ __host__ __device__ constexpr int WCLS(int a) { return a == 0 ? 0 : (a <= 4 ? 1 
 
 // Per-case constants in compute precision.
 template <typename Real> struct K {
-  Real rho0;
-  Real wr[3];  // w rho0 per weight class
-  Real sc[3];  // storage scale per weight class (DEV)
+  Real rho0;   // reference density: sum of the reference values (0 for CODEC_ABS)
+  Real c[3];   // reference value per weight class (CODEC_OFFSET)
+  Real sc[3];  // storage scale per weight class (CODEC_SCALED)
   Real isc[3]; // 1 / storage scale
 };
 
-// Deviation-storage modes compute on d = f_tilde - w rho0 (decode: d = s x);
-// absolute-storage modes compute on f_tilde itself, i.e. with reference
-// density 0 (decode: identity), which saves the offset add per value.
+// Stored value -> value the arithmetic works on (see the CODEC_* list).
 template <int ST, typename Real, typename T>
 __device__ __forceinline__ Real decode(T raw, int a, const K<Real> &k) {
   Real v = to_real(raw);
-  if constexpr (StoreT<ST>::DEV)
+  if constexpr (StoreT<ST>::CODEC == CODEC_SCALED)
     return v * k.sc[WCLS(a)];
+  else if constexpr (StoreT<ST>::CODEC == CODEC_OFFSET)
+    return v - k.c[WCLS(a)];
+  else
+    return v;
+}
+// ... and back.
+template <int ST, typename Real>
+__device__ __forceinline__ Real encode(Real v, int a, const K<Real> &k) {
+  if constexpr (StoreT<ST>::CODEC == CODEC_SCALED)
+    return v * k.isc[WCLS(a)];
+  else if constexpr (StoreT<ST>::CODEC == CODEC_OFFSET)
+    return v + k.c[WCLS(a)];
   else
     return v;
 }
@@ -164,17 +215,50 @@ __device__ __forceinline__ Real deq_of(int a, Real rp, Real rho, Real Ux, Real U
   return Real(WGT(a)) * (rp + rho * P);
 }
 
-// Moments of a 9-vector of deviations: rho' = sum d, U = (sum e d) / rho.
+// Moments of a 9-vector of deviations: rho' = sum d, m = sum e d, U = m / rho.
 template <typename Real>
 __device__ __forceinline__ void moments(const Real (&d)[9], Real rho0, Real &rp, Real &rho,
-                                        Real &Ux, Real &Uy) {
+                                        Real &mx, Real &my, Real &Ux, Real &Uy) {
   rp = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-  Real mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-  Real my = (d[2] - d[4]) + (d[5] - d[8]) + (d[6] - d[7]);
+  mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+  my = (d[2] - d[4]) + (d[5] - d[8]) + (d[6] - d[7]);
   rho = rho0 + rp;
   Real ri = rcp(rho);
   Ux = mx * ri;
   Uy = my * ri;
+}
+template <typename Real>
+__device__ __forceinline__ void moments(const Real (&d)[9], Real rho0, Real &rp, Real &rho,
+                                        Real &Ux, Real &Uy) {
+  Real mx, my;
+  moments(d, rho0, rp, rho, mx, my, Ux, Uy);
+}
+
+// Cell-stage equilibrium deviation d_eq = W (rho' + rho Q) + G (e . m) with
+// the exact-sum coefficients of EqCoef (Eq. equilibrium; P = 3 e.U + Q and
+// rho U = m).  Q is even in e, so one value serves a direction and its
+// opposite.
+template <typename Real>
+__device__ __forceinline__ void cell_deq(Real rp, Real rho, Real mx, Real my, Real Ux, Real Uy,
+                                         Real (&deq)[9]) {
+  using C = EqCoef<Real>;
+  const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
+  const Real up = Ux + Uy, um = Ux - Uy;
+  const Real Qx = Ux * (Real(4.5) * Ux) - u15, Qy = Uy * (Real(4.5) * Uy) - u15;
+  const Real Qp = up * (Real(4.5) * up) - u15, Qm = um * (Real(4.5) * um) - u15;
+  const Real r0 = C::W0 * rho, r1 = C::W1 * rho, r2 = C::W2 * rho;
+  const Real p0 = C::W0 * rp, p1 = C::W1 * rp, p2 = C::W2 * rp;
+  const Real gx = C::G1 * mx, gy = C::G1 * my;
+  const Real gp = C::G2 * (mx + my), gm = C::G2 * (mx - my);
+  deq[0] = p0 - r0 * u15;
+  deq[1] = r1 * Qx + (p1 + gx);
+  deq[3] = r1 * Qx + (p1 - gx);
+  deq[2] = r1 * Qy + (p1 + gy);
+  deq[4] = r1 * Qy + (p1 - gy);
+  deq[5] = r2 * Qp + (p2 + gp); // e = (+1, +1)
+  deq[7] = r2 * Qp + (p2 - gp); // e = (-1, -1)
+  deq[8] = r2 * Qm + (p2 + gm); // e = (+1, -1)
+  deq[6] = r2 * Qm + (p2 - gm); // e = (-1, +1)
 }
 
 // Ghost rule for one ghost cell from the first (p1) and second (p2) inner cell.
@@ -235,28 +319,32 @@ __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Re
       if (EX(a) * nxo + EY(a) * nyo < 0) fb[a] = rw * f1[a] - Real(WGT(a)) * rho0;
     }
   } else if (kind == DVBE_BC_INFLOW_EQ) {
+    // free stream: the distributions entering the domain are f_eq of the
+    // free-stream state; those leaving keep their reconstructed values
     Real rho = Real(sp.rho), Ux = Real(sp.ux), Uy = Real(sp.uy);
     Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) fb[a] = deq_of<Real>(a, rho - rho0, rho, Ux, Uy, u15);
+    for (int a = 1; a < 9; ++a)
+      if (EX(a) * nxo + EY(a) * nyo < 0) fb[a] = deq_of<Real>(a, rho - rho0, rho, Ux, Uy, u15);
   }
 }
 
 // DUGKS: face moments of f_bar, f_eq there and f = p f_bar + q f_eq for the
 // directions crossing the face (AXIS 0: x-face, e_x != 0; 1: y-face).
+// f = f_bar + q (f_eq - f_bar) in increment form (see stage_row).
 template <typename Real, int AXIS>
-__device__ __forceinline__ void dugks_face(Real (&fb)[9], Real rho0, Real p, Real qw1, Real qw2) {
+__device__ __forceinline__ void dugks_face(Real (&fb)[9], Real rho0, Real q, Real w1, Real w2) {
   Real rp, rho, Ux, Uy;
   moments(fb, rho0, rp, rho, Ux, Uy);
   const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
-  // q f_eq - q w rref = q w (rho' + rho P), q w folded per weight class
-  const Real qr1 = qw1 * rho, qp1 = qw1 * rp, qr2 = qw2 * rho, qp2 = qw2 * rp;
+  const Real r1 = w1 * rho, p1 = w1 * rp, r2 = w2 * rho, p2 = w2 * rp;
 #pragma unroll
   for (int a = 1; a < 9; ++a) {
     if ((AXIS == 0 ? EX(a) : EY(a)) != 0) {
       const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
       const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
-      fb[a] = p * fb[a] + (a <= 4 ? qr1 * Pq + qp1 : qr2 * Pq + qp2);
+      const Real deq = a <= 4 ? r1 * Pq + p1 : r2 * Pq + p2;
+      fb[a] = fb[a] + q * (deq - fb[a]);
     }
   }
 }
@@ -405,7 +493,7 @@ template <int SCHEME, int ST> struct Strip {
   K<Real> k;
   int lane, i, nx, ny, i0, xs, xwrapW;
   bool valid, per_x, per_y, touchW, touchE, out_lane, wrapW, wrapE;
-  Real a_phi, b_phi, p_face, qw1, qw2; // qw1/2 = q times the axis / diagonal weight
+  Real b_phi, q_face;
   // x-face coefficients of this lane: right part of its west face, left part
   // of its east face; tangential / update factors of its column.
   Real cR[3], cL[3], tR0, tL0, txc, cxu;
@@ -413,6 +501,7 @@ template <int SCHEME, int ST> struct Strip {
   Real kx1, kx2, ky1, ky2, kxy;
   int segS, segN;
   T *fout;
+  unsigned pitch, plane; // copies of the layout (the argument block is not re-read per row)
   bool bad;
   // row pipeline of this warp
   uint32_t sbase, bbase, txbytes;
@@ -499,19 +588,25 @@ template <int SCHEME, int ST> struct Strip {
     segN = per_y ? 0 : A.segid[3][icc];
     // reference density of the arithmetic: rho0 for deviation storage, 0 for
     // absolute storage
-    k.rho0 = StoreT<ST>::DEV ? Real(A.rho0) : Real(0);
+    constexpr int CODEC = StoreT<ST>::CODEC;
+    k.rho0 = CODEC == CODEC_ABS ? Real(0) : Real(A.rho0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double w = c == 0 ? WGT(0) : (c == 1 ? WGT(1) : WGT(5));
-      k.wr[c] = Real(0);
-      k.sc[c] = StoreT<ST>::DEV ? Real(A.dev_sigma * w * A.rho0) : Real(1);
-      k.isc[c] = StoreT<ST>::DEV ? Real(1.0 / (A.dev_sigma * w * A.rho0)) : Real(1);
+      k.c[c] = Real(0);
+      k.sc[c] = CODEC == CODEC_SCALED ? Real(A.dev_scale[c]) : Real(1);         // a power of two
+      k.isc[c] = CODEC == CODEC_SCALED ? Real(1.0 / A.dev_scale[c]) : Real(1);  // exact inverse
     }
-    a_phi = Real(A.a_phi);
+    if constexpr (CODEC == CODEC_OFFSET) {
+      // c = W rho0 (exact-sum weights): exact when rho0 is a power of two;
+      // otherwise rho0 is replaced by the sum of the rounded c
+      using C = EqCoef<Real>;
+      k.c[0] = Real(C::W0 * A.rho0);
+      k.c[1] = Real(C::W1 * A.rho0);
+      k.c[2] = Real(C::W2 * A.rho0);
+      k.rho0 = Real(double(k.c[0]) + 4.0 * double(k.c[1]) + 4.0 * double(k.c[2]));
+    }
     b_phi = Real(A.b_phi);
-    p_face = Real(A.p_face);
-    qw1 = Real(A.q_face * WGT(1));
-    qw2 = Real(A.q_face * WGT(5));
+    q_face = Real(A.q_face);
     if constexpr (FD) {
       Real nux = Real(A.fd_nux), nuy = Real(A.fd_nuy);
       kx1 = Real(0.5) * nux;
@@ -521,6 +616,8 @@ template <int SCHEME, int ST> struct Strip {
       kxy = Real(0.25) * nux * nuy;
     }
     fout = (T *)A.fout;
+    pitch = (unsigned)A.pitch;
+    plane = (unsigned)A.plane;
   }
 
   // ---- row pipeline: fetch number q of this strip is logical row Fa + q
@@ -583,28 +680,21 @@ template <int SCHEME, int ST> struct Strip {
   }
 
   // Cell stage of a staged row r, then the x ghosts:
-  // phi = a d + b w (rho' + rho P) with b w folded per weight class.
+  // phi = d + b (d_eq - d), d_eq from cell_deq (mass and momentum exact up to
+  // unbiased rounding).  The increment form keeps a state at equilibrium
+  // exactly in place: with rounded coefficients a d + b d_eq would shift it
+  // by (a + b - 1) d every step.
   template <bool INT>
   __device__ __forceinline__ void stage_row(int r, uint32_t stage, Real (&phi)[9]) {
     Real d[9];
     read_row<INT>(stage, d);
-    Real rp, rho, Ux, Uy;
-    moments(d, k.rho0, rp, rho, Ux, Uy);
+    Real rp, rho, mx, my, Ux, Uy;
+    moments(d, k.rho0, rp, rho, mx, my, Ux, Uy);
     bad |= valid && !(rho > Real(0) && rho < Real(1e30));
-    const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
-    Real cr[3], cp[3];
+    Real deq[9];
+    cell_deq(rp, rho, mx, my, Ux, Uy, deq);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const Real bw = b_phi * Real(c == 0 ? WGT(0) : (c == 1 ? WGT(1) : WGT(5)));
-      cr[c] = bw * rho;
-      cp[c] = bw * rp;
-    }
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
-      const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
-      phi[a] = a_phi * d[a] + (cr[WCLS(a)] * Pq + cp[WCLS(a)]);
-    }
+    for (int a = 0; a < 9; ++a) phi[a] = d[a] + b_phi * (deq[a] - d[a]);
     if (!INT && (touchW || touchE)) ghost_x(r, phi);
   }
 
@@ -659,7 +749,7 @@ template <int SCHEME, int ST> struct Strip {
         face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
       }
     }
-    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, p_face, qw1, qw2);
+    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, q_face, Real(WGT(1)), Real(WGT(5)));
   }
 
   // Flux values of the y-face kf (between rows kf-1 and kf) at this column;
@@ -690,23 +780,23 @@ template <int SCHEME, int ST> struct Strip {
       const int side = kf == 0 ? 2 : 3;
       face_bc<Real>(A.seg[side][side == 2 ? segS : segN], 0, side == 2 ? -1 : 1, k.rho0, F);
     }
-    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, p_face, qw1, qw2);
+    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, q_face, Real(WGT(1)), Real(WGT(5)));
   }
 
   __device__ __forceinline__ void store_row(int j, const Real (&v)[9]) {
     // element offsets fit in 32 bits: buffers are limited to 2^31 elements
-    const unsigned off = (unsigned)j * (unsigned)A.pitch + (unsigned)min(max(i, 0), nx - 1);
-    const unsigned plane = (unsigned)A.plane;
+    const unsigned off = (unsigned)j * pitch + (unsigned)min(max(i, 0), nx - 1);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const Real x = StoreT<ST>::DEV ? v[a] * k.isc[WCLS(a)] : v[a];
+      const Real x = encode<ST, Real>(v[a], a, k);
       st_pred(fout + (off + a * plane), x, out_lane);
     }
   }
 
   // One row of the finite-volume update.  DUGKS needs f_tilde^+ of the cell,
-  // recomputed from the staged deviations d and phi = f_bar^+ as
-  // f_tilde^+ = (4 phi - d) / 3 (the two transforms of Sec 2.2 combined).
+  // recomputed from the staged values d and phi = f_bar^+ as
+  // f_tilde^+ = (4 phi - d) / 3 = phi + (phi - d) / 3 (the two transforms of
+  // Sec 2.2 combined; the increment form keeps equilibrium exact).
   template <bool INT>
   __device__ __forceinline__ void update_fv(int j, Real cyu, uint32_t stage, const Real (&Pb)[9],
                                             const Real (&FW)[9], const Real (&FS)[9],
@@ -716,7 +806,7 @@ template <int SCHEME, int ST> struct Strip {
       Real d[9];
       read_row<INT>(stage, d);
 #pragma unroll
-      for (int a = 0; a < 9; ++a) v[a] = (Real(4) * Pb[a] - d[a]) * Real(1.0 / 3.0);
+      for (int a = 0; a < 9; ++a) v[a] = Pb[a] + (Pb[a] - d[a]) * Real(1.0 / 3.0);
     } else {
 #pragma unroll
       for (int a = 0; a < 9; ++a) v[a] = Pb[a];
