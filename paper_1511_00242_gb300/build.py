@@ -39,7 +39,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL")
+KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL",
+         "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL")
 
 
 def _flags():

@@ -55,7 +55,7 @@ static dvbe_status batch_tables(dvbe_batch b) {
     const int base = g == 0 ? 0 : b->ngroup[0];
     for (int k = 0; k < b->ngroup[g]; ++k) {
       CaseArgs &a = b->args[b->order[base + k]];
-      set_strips(a, b->launch.strip_rows);
+      set_strips(a, b->launch.strip_rows, b->store);
       prefix[g * (size_t)(b->n + 1) + k] = acc;
       acc += (long long)a.strips_x * a.strips_y;
     }

@@ -42,7 +42,7 @@ void *dmalloc(size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 dvbe_status build_problem(const dvbe_params *p, Problem &pb);
 dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cudaStream_t s);
-void set_strips(CaseArgs &a, int H);
+void set_strips(CaseArgs &a, int H, int store);
 FieldView view_of(const Problem &pb, void *f);
 int sm_count();
 dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStream_t s,

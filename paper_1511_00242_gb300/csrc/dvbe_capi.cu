@@ -361,9 +361,9 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   return DVBE_OK;
 }
 
-void set_strips(CaseArgs &a, int H) {
+void set_strips(CaseArgs &a, int H, int store) {
   a.H = H;
-  a.strips_x = (a.nx + kStripCols - 1) / kStripCols;
+  a.strips_x = (a.nx + strip_cols(store) - 1) / strip_cols(store);
   a.strips_y = (a.ny + H - 1) / H;
 }
 
@@ -422,8 +422,8 @@ dvbe_status make_tensor_maps(const Problem &pb, void *f, CUtensorMap *main_map,
       dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   }
   const int es = pb.elem;
-  // the step kernel stages 34 (FP64), 36 (FP32) or 40 (16-bit) columns per row
-  const cuuint32_t W = es == 8 ? 34 : (es == 4 ? 36 : 40);
+  // columns per staged row of the step kernel
+  const cuuint32_t W = (cuuint32_t)stage_cols(es, lane_cols(pb.store));
   const cuuint64_t dims[3] = {(cuuint64_t)pb.pitch, (cuuint64_t)pb.ny, 9};
   const cuuint64_t strides[2] = {(cuuint64_t)pb.pitch * es, (cuuint64_t)pb.plane * es};
   const cuuint32_t box_main[3] = {W, 1, 9};
@@ -661,7 +661,7 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
     return st;
   }
   s->args.flag = s->flag;
-  set_strips(s->args, s->launch.strip_rows);
+  set_strips(s->args, s->launch.strip_rows, s->pb.store);
   *out = s;
   return DVBE_OK;
 }
@@ -912,7 +912,7 @@ dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in) {
   dvbe_status st = dvbe_sync(s);
   if (st != DVBE_OK && st != DVBE_ERR_DIVERGED) return st;
   s->launch = *in;
-  set_strips(s->args, in->strip_rows);
+  set_strips(s->args, in->strip_rows, s->pb.store);
   drop_graphs(s);
   return DVBE_OK;
 }
@@ -944,7 +944,7 @@ dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
     if (c.strip_rows > 2 * s->pb.ny && c.strip_rows > 16) continue;
     s->launch = c;
     s->launch.graph_chunk = 0;
-    set_strips(s->args, c.strip_rows);
+    set_strips(s->args, c.strip_rows, s->pb.store);
     e = launch_one(s); // warm-up
     if (e != cudaSuccess) break;
     cudaEventRecord(e0, s->stream);
@@ -970,7 +970,7 @@ dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
   dfree(backup, s->stream);
   bestc.graph_chunk = saved.graph_chunk;
   s->launch = bestc;
-  set_strips(s->args, bestc.strip_rows);
+  set_strips(s->args, bestc.strip_rows, s->pb.store);
   drop_graphs(s);
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
   if (best_ms) *best_ms = best;

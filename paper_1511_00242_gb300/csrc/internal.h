@@ -17,8 +17,21 @@ enum StoreMode { ST_F64 = 0, ST_F32 = 1, ST_F32_DEV = 2, ST_F16_DEV = 3, ST_BF16
 // stretched meshes), and BKG as the Lax-Wendroff stencil (Eq. bkgfd).
 enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2 };
 
-// Lanes per warp minus the two halo columns: output columns per warp row.
-constexpr int kStripCols = 30;
+// Strip geometry.  A warp's lanes hold lane_cols adjacent columns each (two
+// for FP32 arithmetic, which then issues paired FP32 instructions; one for
+// FP64); NC halo columns on each side leave strip_cols output columns per
+// warp row.  A staged row holds stage_cols columns from a 16-byte aligned
+// start at or left of the first lane column (the tensor copy needs x * es to
+// be a multiple of 16 bytes).
+constexpr int lane_cols(int store) { return store == ST_F64 ? 1 : 2; }
+constexpr int strip_cols_nc(int nc) { return 30 * nc; }
+constexpr int strip_cols(int store) { return strip_cols_nc(lane_cols(store)); }
+constexpr int stage_cols(int es, int nc) {
+  return ((32 * nc + 16 / es - 1) + 16 / es - 1) / (16 / es) * (16 / es);
+}
+static_assert(stage_cols(8, 1) == 34 && stage_cols(4, 1) == 36 && stage_cols(2, 1) == 40 &&
+                  stage_cols(4, 2) == 68 && stage_cols(2, 2) == 72,
+              "staged row widths");
 
 struct SegParam {
   int kind;   // dvbe_bc_kind
@@ -42,7 +55,7 @@ struct CaseArgs {
   int pitch;       // elements per row
   int nx, ny;
   int per_x, per_y;
-  int strips_x, strips_y, H; // strip decomposition: 30 columns x H rows per warp
+  int strips_x, strips_y, H; // strip decomposition: strip_cols columns x H rows per warp
 
   double rho0;
   double a_phi, b_phi;   // phi = a delta + b delta_eq   (DUGKS: f_bar^+, BKG: f_tilde^+)

@@ -31,24 +31,31 @@
 
 #include "internal.h"
 
-// Blocks of 256 threads the step kernel must fit per SM; sets its register cap.
-// Occupancy target of the step kernel per scheme: blocks of 256 threads per
-// SM, which caps its registers (1: up to 255, 2: 128).  Measured on the
-// 4096^2 Taylor-Green step: DUGKS is fastest at 2 with a rolled row loop,
-// BKG at 1 with the row loop unrolled by three.
+// Occupancy target of the step kernel: blocks of 256 threads per SM, which
+// caps its registers (1: up to 255, 2: 128).  FP64 (one column per lane) per
+// scheme; FP32 arithmetic (two columns per lane) for both schemes.
 #ifndef DVBE_DUGKS_MINB
 #define DVBE_DUGKS_MINB 2
 #endif
 #ifndef DVBE_BKG_MINB
 #define DVBE_BKG_MINB 1
 #endif
-// Inner-strip row loop of each scheme: 1 = unrolled by three (phi rows rotate
-// by renaming), 0 = rolled with register copies.
+#ifndef DVBE_PAIR_MINB
+#define DVBE_PAIR_MINB 1
+#endif
+// Inner-strip row loop: 1 = unrolled by three (phi rows rotate by renaming),
+// 0 = rolled with register copies; FP64 per scheme, then FP32 per scheme.
 #ifndef DVBE_DUGKS_UNROLL
 #define DVBE_DUGKS_UNROLL 0
 #endif
 #ifndef DVBE_BKG_UNROLL
 #define DVBE_BKG_UNROLL 1
+#endif
+#ifndef DVBE_PAIR_DUGKS_UNROLL
+#define DVBE_PAIR_DUGKS_UNROLL 0
+#endif
+#ifndef DVBE_PAIR_BKG_UNROLL
+#define DVBE_PAIR_BKG_UNROLL 0
 #endif
 
 namespace dvbe {
@@ -162,6 +169,71 @@ template <typename T> __device__ __forceinline__ void store_real(T *p, float v) 
   *p = from_realf<T>(v);
 }
 
+// ---- lane vectors -------------------------------------------------------------
+// A lane holds the values of NC adjacent columns: V = double (NC = 1) for FP64
+// arithmetic, V = F2 (NC = 2) for FP32 arithmetic.  F2 arithmetic uses the
+// paired FP32 instructions (add / sub / mul / fma on .f32x2), which do the
+// work of both columns in one issue slot; each component is rounded exactly
+// as the scalar instruction rounds it.
+struct __align__(8) F2 {
+  float x, y;
+  F2() = default;
+  __device__ __forceinline__ F2(float s) : x(s), y(s) {}
+  __device__ __forceinline__ F2(float a, float b) : x(a), y(b) {}
+};
+__device__ __forceinline__ float2 f2v(F2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ F2 v2f(float2 a) { return F2(a.x, a.y); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return v2f(__fadd2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return v2f(__fmul2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 r;
+  asm("{ .reg .b64 pa, pb, pc;\n"
+      "mov.b64 pa, {%2, %3}; mov.b64 pb, {%4, %5};\n"
+      "sub.rn.f32x2 pc, pa, pb; mov.b64 {%0, %1}, pc; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
+  return v2f(__ffma2_rn(f2v(a), f2v(b), f2v(c)));
+}
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+
+// Value of the column to the left / right (one and two columns away) of each
+// of this lane's columns; lanes hold consecutive columns in order.
+__device__ __forceinline__ double shift_l(double v) { return __shfl_up_sync(kFull, v, 1); }
+__device__ __forceinline__ double shift_r(double v) { return __shfl_down_sync(kFull, v, 1); }
+__device__ __forceinline__ double shift_l2(double v) { return __shfl_up_sync(kFull, v, 2); }
+__device__ __forceinline__ double shift_r2(double v) { return __shfl_down_sync(kFull, v, 2); }
+__device__ __forceinline__ F2 shift_l(F2 v) { return F2(__shfl_up_sync(kFull, v.y, 1), v.x); }
+__device__ __forceinline__ F2 shift_r(F2 v) { return F2(v.y, __shfl_down_sync(kFull, v.x, 1)); }
+__device__ __forceinline__ F2 shift_l2(F2 v) {
+  return F2(__shfl_up_sync(kFull, v.x, 1), __shfl_up_sync(kFull, v.y, 1));
+}
+__device__ __forceinline__ F2 shift_r2(F2 v) {
+  return F2(__shfl_down_sync(kFull, v.x, 1), __shfl_down_sync(kFull, v.y, 1));
+}
+
+__device__ __forceinline__ double comp(double v, int) { return v; }
+__device__ __forceinline__ float comp(F2 v, int c) { return c ? v.y : v.x; }
+__device__ __forceinline__ void set_comp(double &v, int, double s) { v = s; }
+__device__ __forceinline__ void set_comp(F2 &v, int c, float s) {
+  if (c)
+    v.y = s;
+  else
+    v.x = s;
+}
+
+template <typename Real> struct LaneT;
+template <> struct LaneT<double> {
+  using V = double;
+  static constexpr int NC = 1;
+};
+template <> struct LaneT<float> {
+  using V = F2;
+  static constexpr int NC = 2;
+};
+
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 // Single precision: hardware approximation refined by one Newton-Raphson
 // step r <- r (2 - x r), within about one ulp of 1/x.
@@ -171,22 +243,22 @@ __device__ __forceinline__ float rcp(float x) {
   const float e = fmaf(-x, r, 1.0f);
   return fmaf(r, e, r);
 }
+__device__ __forceinline__ F2 rcp(F2 x) { return F2(rcp(x.x), rcp(x.y)); }
 
 // Weight class of a direction: 0 rest, 1 axis, 2 diagonal.
 __host__ __device__ constexpr int WCLS(int a) { return a == 0 ? 0 : (a <= 4 ? 1 : 2); }
 
-// Per-case constants in compute precision.
-template <typename Real> struct K {
-  Real rho0;   // reference density: sum of the reference values (0 for CODEC_ABS)
-  Real c[3];   // reference value per weight class (CODEC_OFFSET)
-  Real sc[3];  // storage scale per weight class (CODEC_SCALED)
-  Real isc[3]; // 1 / storage scale
+// Per-case constants in compute precision, one copy per lane column.
+template <typename V> struct K {
+  V rho0;   // reference density: sum of the reference values (0 for CODEC_ABS)
+  V c[3];   // reference value per weight class (CODEC_OFFSET)
+  V sc[3];  // storage scale per weight class (CODEC_SCALED)
+  V isc[3]; // 1 / storage scale
 };
 
-// Stored value -> value the arithmetic works on (see the CODEC_* list).
-template <int ST, typename Real, typename T>
-__device__ __forceinline__ Real decode(T raw, int a, const K<Real> &k) {
-  Real v = to_real(raw);
+// Stored value (converted to compute precision) -> value the arithmetic works
+// on (see the CODEC_* list).
+template <int ST, typename V> __device__ __forceinline__ V decode(V v, int a, const K<V> &k) {
   if constexpr (StoreT<ST>::CODEC == CODEC_SCALED)
     return v * k.sc[WCLS(a)];
   else if constexpr (StoreT<ST>::CODEC == CODEC_OFFSET)
@@ -195,8 +267,7 @@ __device__ __forceinline__ Real decode(T raw, int a, const K<Real> &k) {
     return v;
 }
 // ... and back.
-template <int ST, typename Real>
-__device__ __forceinline__ Real encode(Real v, int a, const K<Real> &k) {
+template <int ST, typename V> __device__ __forceinline__ V encode(V v, int a, const K<V> &k) {
   if constexpr (StoreT<ST>::CODEC == CODEC_SCALED)
     return v * k.isc[WCLS(a)];
   else if constexpr (StoreT<ST>::CODEC == CODEC_OFFSET)
@@ -207,7 +278,7 @@ __device__ __forceinline__ Real encode(Real v, int a, const K<Real> &k) {
 
 // delta_eq_alpha = f_eq_alpha - w rref = w (rho' + rho P(e.U)) with rho' =
 // rho - rref, P = 3 eU + 4.5 eU^2 - 1.5 |U|^2 and U = u / c (Eq. equilibrium,
-// c_s^2 = c^2/3).  rref is rho0 for deviation storage and 0 otherwise.
+// c_s^2 = c^2/3).  rref is rho0 for deviation arithmetic and 0 otherwise.
 template <typename Real>
 __device__ __forceinline__ Real deq_of(int a, Real rp, Real rho, Real Ux, Real Uy, Real u15) {
   Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
@@ -216,49 +287,42 @@ __device__ __forceinline__ Real deq_of(int a, Real rp, Real rho, Real Ux, Real U
 }
 
 // Moments of a 9-vector of deviations: rho' = sum d, m = sum e d, U = m / rho.
-template <typename Real>
-__device__ __forceinline__ void moments(const Real (&d)[9], Real rho0, Real &rp, Real &rho,
-                                        Real &mx, Real &my, Real &Ux, Real &Uy) {
+template <typename V>
+__device__ __forceinline__ void moments(const V (&d)[9], V rho0, V &rp, V &rho, V &mx, V &my,
+                                        V &Ux, V &Uy) {
   rp = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
   mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
   my = (d[2] - d[4]) + (d[5] - d[8]) + (d[6] - d[7]);
   rho = rho0 + rp;
-  Real ri = rcp(rho);
+  const V ri = rcp(rho);
   Ux = mx * ri;
   Uy = my * ri;
-}
-template <typename Real>
-__device__ __forceinline__ void moments(const Real (&d)[9], Real rho0, Real &rp, Real &rho,
-                                        Real &Ux, Real &Uy) {
-  Real mx, my;
-  moments(d, rho0, rp, rho, mx, my, Ux, Uy);
 }
 
 // Cell-stage equilibrium deviation d_eq = W (rho' + rho Q) + G (e . m) with
 // the exact-sum coefficients of EqCoef (Eq. equilibrium; P = 3 e.U + Q and
 // rho U = m).  Q is even in e, so one value serves a direction and its
 // opposite.
-template <typename Real>
-__device__ __forceinline__ void cell_deq(Real rp, Real rho, Real mx, Real my, Real Ux, Real Uy,
-                                         Real (&deq)[9]) {
+template <typename Real, typename V>
+__device__ __forceinline__ void cell_deq(V rp, V rho, V mx, V my, V Ux, V Uy, V (&deq)[9]) {
   using C = EqCoef<Real>;
-  const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
-  const Real up = Ux + Uy, um = Ux - Uy;
-  const Real Qx = Ux * (Real(4.5) * Ux) - u15, Qy = Uy * (Real(4.5) * Uy) - u15;
-  const Real Qp = up * (Real(4.5) * up) - u15, Qm = um * (Real(4.5) * um) - u15;
-  const Real r0 = C::W0 * rho, r1 = C::W1 * rho, r2 = C::W2 * rho;
-  const Real p0 = C::W0 * rp, p1 = C::W1 * rp, p2 = C::W2 * rp;
-  const Real gx = C::G1 * mx, gy = C::G1 * my;
-  const Real gp = C::G2 * (mx + my), gm = C::G2 * (mx - my);
-  deq[0] = p0 - r0 * u15;
-  deq[1] = r1 * Qx + (p1 + gx);
-  deq[3] = r1 * Qx + (p1 - gx);
-  deq[2] = r1 * Qy + (p1 + gy);
-  deq[4] = r1 * Qy + (p1 - gy);
-  deq[5] = r2 * Qp + (p2 + gp); // e = (+1, +1)
-  deq[7] = r2 * Qp + (p2 - gp); // e = (-1, -1)
-  deq[8] = r2 * Qm + (p2 + gm); // e = (+1, -1)
-  deq[6] = r2 * Qm + (p2 - gm); // e = (-1, +1)
+  const V nu15 = V(Real(-1.5)) * vfma(Ux, Ux, Uy * Uy);
+  const V up = Ux + Uy, um = Ux - Uy, h = V(Real(4.5));
+  const V Qx = vfma(Ux, h * Ux, nu15), Qy = vfma(Uy, h * Uy, nu15);
+  const V Qp = vfma(up, h * up, nu15), Qm = vfma(um, h * um, nu15);
+  const V r0 = V(C::W0) * rho, r1 = V(C::W1) * rho, r2 = V(C::W2) * rho;
+  const V p0 = V(C::W0) * rp, p1 = V(C::W1) * rp, p2 = V(C::W2) * rp;
+  const V gx = V(C::G1) * mx, gy = V(C::G1) * my;
+  const V gp = V(C::G2) * (mx + my), gm = V(C::G2) * (mx - my);
+  deq[0] = vfma(r0, nu15, p0);
+  deq[1] = vfma(r1, Qx, p1 + gx);
+  deq[3] = vfma(r1, Qx, p1 - gx);
+  deq[2] = vfma(r1, Qy, p1 + gy);
+  deq[4] = vfma(r1, Qy, p1 - gy);
+  deq[5] = vfma(r2, Qp, p2 + gp); // e = (+1, +1)
+  deq[7] = vfma(r2, Qp, p2 - gp); // e = (-1, -1)
+  deq[8] = vfma(r2, Qm, p2 + gm); // e = (+1, -1)
+  deq[6] = vfma(r2, Qm, p2 - gm); // e = (-1, +1)
 }
 
 // Ghost rule for one ghost cell from the first (p1) and second (p2) inner cell.
@@ -285,8 +349,8 @@ __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho
 }
 
 // Boundary face treatment (Sec 2.5) on face values fb (deviations), outward
-// normal (nx_o, ny_o) of the fluid.  NEED(a) tells which directions the
-// caller has computed (BKG skips the ones with zero normal velocity).
+// normal (nx_o, ny_o) of the fluid.  Only the directions crossing the face
+// are read or written.
 template <typename Real>
 __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Real rho0,
                                         Real (&fb)[9]) {
@@ -330,22 +394,25 @@ __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Re
 }
 
 // DUGKS: face moments of f_bar, f_eq there and f = p f_bar + q f_eq for the
-// directions crossing the face (AXIS 0: x-face, e_x != 0; 1: y-face).
-// f = f_bar + q (f_eq - f_bar) in increment form (see stage_row).
-template <typename Real, int AXIS>
-__device__ __forceinline__ void dugks_face(Real (&fb)[9], Real rho0, Real q, Real w1, Real w2) {
-  Real rp, rho, Ux, Uy;
-  moments(fb, rho0, rp, rho, Ux, Uy);
-  const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
-  const Real r1 = w1 * rho, p1 = w1 * rp, r2 = w2 * rho, p2 = w2 * rp;
+// directions crossing the face (AXIS 0: x-face, e_x != 0; 1: y-face), in
+// increment form f = f_bar + q (f_eq - f_bar) (see stage_row).  For
+// e.U = +-s, P = s (4.5 s +- 3) - 1.5 |U|^2.
+template <typename Real, int AXIS, typename V>
+__device__ __forceinline__ void dugks_face(V (&fb)[9], V rho0, V q) {
+  V rp, rho, mx, my, Ux, Uy;
+  moments(fb, rho0, rp, rho, mx, my, Ux, Uy);
+  const V nu15 = V(Real(-1.5)) * vfma(Ux, Ux, Uy * Uy);
+  const V w1 = V(Real(WGT(1))), w2 = V(Real(WGT(5)));
+  const V r1 = w1 * rho, p1 = w1 * rp, r2 = w2 * rho, p2 = w2 * rp;
+  const V up = Ux + Uy, um = Ux - Uy, h = V(Real(4.5)), t3 = V(Real(3)), m3 = V(Real(-3));
 #pragma unroll
   for (int a = 1; a < 9; ++a) {
-    if ((AXIS == 0 ? EX(a) : EY(a)) != 0) {
-      const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
-      const Real Pq = eU * (Real(3) + Real(4.5) * eU) - u15;
-      const Real deq = a <= 4 ? r1 * Pq + p1 : r2 * Pq + p2;
-      fb[a] = fb[a] + q * (deq - fb[a]);
-    }
+    if ((AXIS == 0 ? EX(a) : EY(a)) == 0) continue;
+    const V s = (a == 1 || a == 3) ? Ux : ((a == 2 || a == 4) ? Uy : ((a == 5 || a == 7) ? up : um));
+    const bool pos = a == 1 || a == 2 || a == 5 || a == 8;
+    const V P = vfma(s, vfma(h, s, pos ? t3 : m3), nu15);
+    const V deq = a <= 4 ? vfma(r1, P, p1) : vfma(r2, P, p2);
+    fb[a] = vfma(q, deq - fb[a], fb[a]);
   }
 }
 
@@ -455,17 +522,64 @@ __device__ __forceinline__ void st_pred(__nv_bfloat16 *p, float v, bool on) {
                : "memory");
 }
 
+// One lane's NC adjacent values of a staged row (interior strips, where the
+// NC columns are aligned: 8 bytes for FP32 pairs, 4 for 16-bit pairs) ...
+__device__ __forceinline__ double ld_lane(uint32_t a, const double *) { return lds<double>(a); }
+__device__ __forceinline__ F2 ld_lane(uint32_t a, const float *) {
+  float x, y;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+  return F2(x, y);
+}
+__device__ __forceinline__ F2 ld_lane(uint32_t a, const __half *) {
+  unsigned v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  __half2 h;
+  memcpy(&h, &v, 4);
+  const float2 f = __half22float2(h);
+  return F2(f.x, f.y);
+}
+__device__ __forceinline__ F2 ld_lane(uint32_t a, const __nv_bfloat16 *) {
+  unsigned v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  __nv_bfloat162 h;
+  memcpy(&h, &v, 4);
+  const float2 f = __bfloat1622float2(h);
+  return F2(f.x, f.y);
+}
+// ... and the predicated store of them.
+__device__ __forceinline__ void st_lane(double *p, double v, bool on) { st_pred(p, v, on); }
+__device__ __forceinline__ void st_lane(float *p, F2 v, bool on) {
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %3, 0; @q st.global.v2.f32 [%0], {%1, %2}; }" ::"l"(p),
+               "f"(v.x), "f"(v.y), "r"((int)on)
+               : "memory");
+}
+__device__ __forceinline__ void st_lane(__half *p, F2 v, bool on) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
+  unsigned b;
+  memcpy(&b, &h, 4);
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.b32 [%0], %1; }" ::"l"(p), "r"(b),
+               "r"((int)on)
+               : "memory");
+}
+__device__ __forceinline__ void st_lane(__nv_bfloat16 *p, F2 v, bool on) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  unsigned b;
+  memcpy(&b, &h, 4);
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.global.b32 [%0], %1; }" ::"l"(p), "r"(b),
+               "r"((int)on)
+               : "memory");
+}
+
 // Waits longer than this many polls are treated as a failure: the warp sets
 // bit 1 of the case flag and abandons its work (the host reports a timeout).
 constexpr uint32_t kSpinLimit = 1u << 24;
 
-// Shared-memory geometry of one warp's row pipeline for element size ES.
-template <int ES> struct Pipe {
-  // columns per staged row: covers the 32 lanes' columns from a 16-byte
-  // aligned start (the tensor copy needs x * ES to be a multiple of 16)
-  static constexpr int W = ES == 8 ? 34 : (ES == 4 ? 36 : 40);
-  static constexpr int WW = 16 / ES; // columns of the periodic-wrap copies
-  static constexpr int NS = 5;       // stages: rows j, j+1 held, three in flight
+// Shared-memory geometry of one warp's row pipeline for element size ES and
+// NC columns per lane.
+template <int ES, int NC> struct Pipe {
+  static constexpr int W = stage_cols(ES, NC); // columns per staged row
+  static constexpr int WW = 16 / ES;           // columns of the periodic-wrap copies
+  static constexpr int NS = 5;                 // stages: rows j, j+1 held, three in flight
   static constexpr int MAINB = ((9 * W * ES + 127) / 128) * 128;
   // periodic-wrap copies: a 9 x 16-byte box each (fields packed 16 bytes
   // apart); every tensor-copy destination sits on a 128-byte boundary
@@ -476,6 +590,8 @@ template <int ES> struct Pipe {
   static_assert(MAINB % 128 == 0 && WRAPB % 128 == 0 && STAGEB % 128 == 0 && WARPB % 128 == 0,
                 "shared-memory layout must keep tensor-copy destinations 128-byte aligned");
   static_assert(9 * W * ES <= MAINB && 9 * 16 <= WRAPB && NS * 8 <= 128, "buffer sizes");
+  // pair loads of a staged row need the field stride to keep their alignment
+  static_assert((W * ES) % (NC * ES) == 0, "field stride of a staged row");
 };
 
 // ---- the strip ---------------------------------------------------------------
@@ -484,29 +600,36 @@ template <int SCHEME, int ST> struct Strip {
   using S = StoreT<ST>;
   using Real = typename S::Real;
   using T = typename S::T;
-  using P = Pipe<(int)sizeof(T)>;
+  using V = typename LaneT<Real>::V;
+  static constexpr int NC = LaneT<Real>::NC;   // columns per lane
+  static constexpr int COLS = strip_cols_nc(NC); // output columns per strip
+  static constexpr int ES = (int)sizeof(T);
+  using P = Pipe<ES, NC>;
   static constexpr bool DUG = SCHEME == SC_DUGKS;
   static constexpr bool FD = SCHEME == SC_BKG_FD;
-  static constexpr int ES = (int)sizeof(T);
 
   const CaseArgs &A;
-  K<Real> k;
-  int lane, i, nx, ny, i0, xs, xwrapW;
-  bool valid, per_x, per_y, touchW, touchE, out_lane, wrapW, wrapE;
-  Real b_phi, q_face;
-  // x-face coefficients of this lane: right part of its west face, left part
-  // of its east face; tangential / update factors of its column.
-  Real cR[3], cL[3], tR0, tL0, txc, cxu;
+  K<V> k;
+  int lane, nx, ny, i0, c0, xs, xwrapW;
+  int col[NC];       // this lane's columns c0, c0 + 1, ...
+  bool valid[NC];    // column holds a cell or a ghost
+  bool outc[NC];     // column is an output of this strip
+  bool wrapc[NC];    // column comes from a periodic wrap copy
+  uint32_t offc[NC]; // byte offset of each column inside a stage (boundary strips)
+  uint32_t lds_off;  // byte offset of the first column (inner strips: one aligned load)
+  bool per_x, per_y, touchW, touchE, wrapW, wrapE, out_lane;
+  V b_phi, q_face;
+  // x-face coefficients of this lane's columns: right part of the west face,
+  // left part of the east face; tangential / update factors of the column.
+  V cR[3], cL[3], tR0, tL0, txc, ntxc, cxu, ncxu;
   // BKG-FD stencil factors
   Real kx1, kx2, ky1, ky2, kxy;
-  int segS, segN;
+  int segS[NC], segN[NC];
   T *fout;
   unsigned pitch, plane; // copies of the layout (the argument block is not re-read per row)
   bool bad;
   // row pipeline of this warp
   uint32_t sbase, bbase, txbytes;
-  uint32_t lds_off; // byte offset of this lane's first value inside a stage
-  bool wrap_lane;   // reads a periodic wrap copy (fields 16 bytes apart)
   // Fetches are issued and waited for in order through the NS stages, so
   // every stage in one pass of the ring completes a phase of the same parity:
   // islot / cslot are the stages of the next issue / wait and cpar the parity
@@ -544,69 +667,79 @@ template <int SCHEME, int ST> struct Strip {
     ny = A.ny;
     per_x = A.per_x;
     per_y = A.per_y;
-    i0 = sx * kStripCols;
-    i = i0 - 1 + lane;
-    valid = (i >= 0 && i < nx) || (per_x && (i == -1 || i == nx));
+    i0 = sx * COLS;
+    // the strip's lanes hold columns i0 - NC .. i0 + COLS + NC - 1: NC halo
+    // columns on each side, of which only the one next to the outputs is used
+    c0 = i0 - NC + NC * lane;
     touchW = !per_x && i0 == 0;
-    touchE = !per_x && i0 + kStripCols >= nx;
+    touchE = !per_x && i0 + COLS >= nx;
     wrapW = per_x && i0 == 0;
-    wrapE = per_x && i0 + kStripCols >= nx;
-    out_lane = lane >= 1 && lane <= kStripCols && i < nx;
-    // staged columns: [xs, xs + W) with xs the aligned start at or left of i0 - 1
+    wrapE = per_x && i0 + COLS >= nx;
+    out_lane = lane >= 1 && lane <= 30; // inner strips: these lanes hold outputs only
+    // staged columns: [xs, xs + W) with xs the aligned start at or left of i0 - NC
     const int al = 16 / ES;
-    xs = (i0 - 1 >= 0) ? ((i0 - 1) / al) * al : -al;
-    lds_off = (uint32_t)((i - xs) * ES);
-    // periodic wrap columns come from the wrap copies: column nx-1 for the
-    // west halo lane, column 0 for the east halo lane
-    wrap_lane = false;
-    if (wrapW && i == -1) {
-      lds_off = (uint32_t)(P::MAINB + (nx - 1 - ((nx - 1) / (16 / ES)) * (16 / ES)) * ES);
-      wrap_lane = true;
-    }
-    if (wrapE && i == nx) {
-      lds_off = (uint32_t)(P::MAINB + P::WRAPB);
-      wrap_lane = true;
-    }
+    xs = (i0 - NC >= 0) ? ((i0 - NC) / al) * al : -al;
+    lds_off = (uint32_t)((c0 - xs) * ES);
+    xwrapW = ((nx - 1) / al) * al;
     txbytes = 9u * P::W * ES + (wrapW ? 9u * 16u : 0u) + (wrapE ? 9u * 16u : 0u);
-    xwrapW = ((nx - 1) / (16 / ES)) * (16 / ES);
-    const int ic = min(max(i, -1), nx);
     const Real *xfth = (const Real *)A.xfth, *xfs = (const Real *)A.xfs;
     const Real *xct = (const Real *)A.xct, *xcu = (const Real *)A.xcu;
-    Real thW = xfth[ic + 1], sW = xfs[ic + 1], thE = xfth[ic + 2], sE = xfs[ic + 2];
-    cR[0] = thW + sW; // e_x = -1
-    cR[1] = thW;
-    cR[2] = thW - sW;
-    cL[0] = (Real(1) - thE) - sE;
-    cL[1] = Real(1) - thE;
-    cL[2] = (Real(1) - thE) + sE;
-    tR0 = thW;
-    tL0 = Real(1) - thE;
-    txc = xct[ic + 1];
-    cxu = xcu[ic + 1];
-    const int icc = min(max(i, 0), nx - 1);
-    segS = per_y ? 0 : A.segid[2][icc];
-    segN = per_y ? 0 : A.segid[3][icc];
-    // reference density of the arithmetic: rho0 for deviation storage, 0 for
-    // absolute storage
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int i = c0 + c;
+      col[c] = i;
+      valid[c] = (i >= 0 && i < nx) || (per_x && (i == -1 || i == nx));
+      outc[c] = i >= i0 && i < i0 + COLS && i < nx;
+      offc[c] = (uint32_t)((i - xs) * ES);
+      wrapc[c] = false;
+      // periodic wrap columns come from the wrap copies: column nx-1 for the
+      // west halo, column 0 for the east halo
+      if (wrapW && i == -1) {
+        offc[c] = (uint32_t)(P::MAINB + (nx - 1 - xwrapW) * ES);
+        wrapc[c] = true;
+      }
+      if (wrapE && i == nx) {
+        offc[c] = (uint32_t)(P::MAINB + P::WRAPB);
+        wrapc[c] = true;
+      }
+      const int ic = min(max(i, -1), nx);
+      const Real thW = xfth[ic + 1], sW = xfs[ic + 1], thE = xfth[ic + 2], sE = xfs[ic + 2];
+      set_comp(cR[0], c, thW + sW); // e_x = -1
+      set_comp(cR[1], c, thW);
+      set_comp(cR[2], c, thW - sW);
+      set_comp(cL[0], c, (Real(1) - thE) - sE);
+      set_comp(cL[1], c, Real(1) - thE);
+      set_comp(cL[2], c, (Real(1) - thE) + sE);
+      set_comp(tR0, c, thW);
+      set_comp(tL0, c, Real(1) - thE);
+      set_comp(txc, c, xct[ic + 1]);
+      set_comp(ntxc, c, -xct[ic + 1]);
+      set_comp(cxu, c, xcu[ic + 1]);
+      set_comp(ncxu, c, -xcu[ic + 1]);
+      const int icc = min(max(i, 0), nx - 1);
+      segS[c] = per_y ? 0 : A.segid[2][icc];
+      segN[c] = per_y ? 0 : A.segid[3][icc];
+    }
+    // reference density of the arithmetic: rho0 for deviation arithmetic, 0 for
+    // FP64 on f_tilde itself
     constexpr int CODEC = StoreT<ST>::CODEC;
-    k.rho0 = CODEC == CODEC_ABS ? Real(0) : Real(A.rho0);
+    k.rho0 = V(CODEC == CODEC_ABS ? Real(0) : Real(A.rho0));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      k.c[c] = Real(0);
-      k.sc[c] = CODEC == CODEC_SCALED ? Real(A.dev_scale[c]) : Real(1);         // a power of two
-      k.isc[c] = CODEC == CODEC_SCALED ? Real(1.0 / A.dev_scale[c]) : Real(1);  // exact inverse
+      k.c[c] = V(Real(0));
+      k.sc[c] = V(CODEC == CODEC_SCALED ? Real(A.dev_scale[c]) : Real(1));        // a power of two
+      k.isc[c] = V(CODEC == CODEC_SCALED ? Real(1.0 / A.dev_scale[c]) : Real(1)); // exact inverse
     }
     if constexpr (CODEC == CODEC_OFFSET) {
       // c = W rho0 (exact-sum weights): exact when rho0 is a power of two;
       // otherwise rho0 is replaced by the sum of the rounded c
       using C = EqCoef<Real>;
-      k.c[0] = Real(C::W0 * A.rho0);
-      k.c[1] = Real(C::W1 * A.rho0);
-      k.c[2] = Real(C::W2 * A.rho0);
-      k.rho0 = Real(double(k.c[0]) + 4.0 * double(k.c[1]) + 4.0 * double(k.c[2]));
+      const Real cw[3] = {Real(C::W0 * A.rho0), Real(C::W1 * A.rho0), Real(C::W2 * A.rho0)};
+      for (int c = 0; c < 3; ++c) k.c[c] = V(cw[c]);
+      k.rho0 = V(Real(double(cw[0]) + 4.0 * double(cw[1]) + 4.0 * double(cw[2])));
     }
-    b_phi = Real(A.b_phi);
-    q_face = Real(A.q_face);
+    b_phi = V(Real(A.b_phi));
+    q_face = V(Real(A.q_face));
     if constexpr (FD) {
       Real nux = Real(A.fd_nux), nuy = Real(A.fd_nuy);
       kx1 = Real(0.5) * nux;
@@ -667,15 +800,20 @@ template <int SCHEME, int ST> struct Strip {
     }
   }
 
-  template <bool INT> __device__ __forceinline__ void read_row(uint32_t stage, Real (&d)[9]) {
-    const uint32_t base = stage + lds_off;
-    if (!INT && (wrapW || wrapE)) { // warp-uniform: only the strips at a periodic x edge
+  template <bool INT> __device__ __forceinline__ void read_row(uint32_t stage, V (&d)[9]) {
+    if (INT) {
+      const uint32_t base = stage + lds_off;
 #pragma unroll
-      for (int a = 0; a < 9; ++a)
-        d[a] = decode<ST, Real>(lds<T>(base + a * (wrap_lane ? 16u : (uint32_t)(P::W * ES))), a, k);
+      for (int a = 0; a < 9; ++a) d[a] = decode<ST>(ld_lane(base + a * P::W * ES, (const T *)nullptr), a, k);
     } else {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) d[a] = decode<ST, Real>(lds<T>(base + a * P::W * ES), a, k);
+      for (int a = 0; a < 9; ++a) {
+        V v;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          set_comp(v, c, to_real(lds<T>(stage + offc[c] + a * (wrapc[c] ? 16u : (uint32_t)(P::W * ES)))));
+        d[a] = decode<ST>(v, a, k);
+      }
     }
   }
 
@@ -685,173 +823,179 @@ template <int SCHEME, int ST> struct Strip {
   // exactly in place: with rounded coefficients a d + b d_eq would shift it
   // by (a + b - 1) d every step.
   template <bool INT>
-  __device__ __forceinline__ void stage_row(int r, uint32_t stage, Real (&phi)[9]) {
-    Real d[9];
+  __device__ __forceinline__ void stage_row(int r, uint32_t stage, V (&phi)[9]) {
+    V d[9];
     read_row<INT>(stage, d);
-    Real rp, rho, mx, my, Ux, Uy;
+    V rp, rho, mx, my, Ux, Uy;
     moments(d, k.rho0, rp, rho, mx, my, Ux, Uy);
-    bad |= valid && !(rho > Real(0) && rho < Real(1e30));
-    Real deq[9];
-    cell_deq(rp, rho, mx, my, Ux, Uy, deq);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) phi[a] = d[a] + b_phi * (deq[a] - d[a]);
+    for (int c = 0; c < NC; ++c) {
+      const Real rc = comp(rho, c);
+      bad |= valid[c] && !(rc > Real(0) && rc < Real(1e30));
+    }
+    V deq[9];
+    cell_deq<Real>(rp, rho, mx, my, Ux, Uy, deq);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) phi[a] = vfma(b_phi, deq[a] - d[a], d[a]);
     if (!INT && (touchW || touchE)) ghost_x(r, phi);
   }
 
-  __device__ __forceinline__ void ghost_x(int r, Real (&phi)[9]) {
-    Real q1[9], q2[9];
+  // Boundary rules are applied per column on scalar copies.
+  __device__ __forceinline__ void get(const V (&v)[9], int c, Real (&s)[9]) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) s[a] = comp(v[a], c);
+  }
+  __device__ __forceinline__ void put(V (&v)[9], int c, const Real (&s)[9]) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) set_comp(v[a], c, s[a]);
+  }
+
+  __device__ __forceinline__ void ghost_x(int r, V (&phi)[9]) {
+    V q1[9], q2[9];
     if (touchW) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        q1[a] = __shfl_down_sync(kFull, phi[a], 1);
-        q2[a] = __shfl_down_sync(kFull, phi[a], 2);
+        q1[a] = shift_r(phi[a]);
+        q2[a] = shift_r2(phi[a]);
       }
-      if (i == -1) apply_ghost<Real, true>(A.seg[0][A.segid[0][r]], Real(A.ext[0]), k.rho0, q1, q2, phi);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (col[c] == -1) {
+          Real s1[9], s2[9], g[9];
+          get(q1, c, s1);
+          get(q2, c, s2);
+          get(phi, c, g);
+          apply_ghost<Real, true>(A.seg[0][A.segid[0][r]], Real(A.ext[0]), comp(k.rho0, 0), s1, s2, g);
+          put(phi, c, g);
+        }
+      }
     }
     if (touchE) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        q1[a] = __shfl_up_sync(kFull, phi[a], 1);
-        q2[a] = __shfl_up_sync(kFull, phi[a], 2);
+        q1[a] = shift_l(phi[a]);
+        q2[a] = shift_l2(phi[a]);
       }
-      if (i == nx) apply_ghost<Real, true>(A.seg[1][A.segid[1][r]], Real(A.ext[1]), k.rho0, q1, q2, phi);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (col[c] == nx) {
+          Real s1[9], s2[9], g[9];
+          get(q1, c, s1);
+          get(q2, c, s2);
+          get(phi, c, g);
+          apply_ghost<Real, true>(A.seg[1][A.segid[1][r]], Real(A.ext[1]), comp(k.rho0, 0), s1, s2, g);
+          put(phi, c, g);
+        }
+      }
     }
   }
 
   // Ghost row from the first (p1) and second (p2) inner rows; side 2 = S, 3 = N.
-  __device__ __forceinline__ void ghost_row(int side, const Real (&p1)[9], const Real (&p2)[9],
-                                            Real (&g)[9]) {
-    const SegParam &sp = A.seg[side][side == 2 ? segS : segN];
-    apply_ghost<Real, false>(sp, Real(A.ext[side]), k.rho0, p1, p2, g);
+  __device__ __forceinline__ void ghost_row(int side, const V (&p1)[9], const V (&p2)[9], V (&g)[9]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      Real s1[9], s2[9], gs[9];
+      get(p1, c, s1);
+      get(p2, c, s2);
+      get(g, c, gs);
+      const SegParam &sp = A.seg[side][side == 2 ? segS[c] : segN[c]];
+      apply_ghost<Real, false>(sp, Real(A.ext[side]), comp(k.rho0, 0), s1, s2, gs);
+      put(g, c, gs);
+    }
   }
 
-  // Flux values of the x-face west of this lane's cell at row j.
+  // Flux values of the x-face west of each of this lane's columns at row j:
+  // f_bar at x_b - h xi by linear reconstruction, left part from the column
+  // to the left (Eqs. eq_char / bkg_fb).
   template <bool INT>
-  __device__ __forceinline__ void xface(int j, Real tyc, const Real (&Pm)[9], const Real (&P0)[9],
-                                        const Real (&Pp)[9], Real (&F)[9]) {
-    const Real tL = tyc * tL0, tR = tyc * tR0;
+  __device__ __forceinline__ void xface(int j, Real tyc, const V (&Pm)[9], const V (&P0)[9],
+                                        const V (&Pp)[9], V (&F)[9]) {
+    const V tL = V(tyc) * tL0, tR = V(tyc) * tR0;
+    const V z = V(Real(0)), mtL = z - tL, mtR = z - tR;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      if (!needx<SCHEME>(a)) continue;
+      if (!needx<SCHEME>(a)) {
+        F[a] = z;
+        continue;
+      }
+      const V PcL = P0[a] * cL[EX(a) + 1];
       if (EY(a) != 0) {
-        const Real dy = Pp[a] - Pm[a];
-        const Real Lp = P0[a] * cL[EX(a) + 1] - Real(EY(a)) * tL * dy;
-        const Real in = __shfl_up_sync(kFull, Lp, 1) - Real(EY(a)) * tR * dy;
-        F[a] = P0[a] * cR[EX(a) + 1] + in;
+        // left part P0 cL - e_y tL dy, right part P0 cR - e_y tR dy
+        const V dy = Pp[a] - Pm[a];
+        const V Lp = vfma(EY(a) > 0 ? mtL : tL, dy, PcL);
+        const V in = vfma(EY(a) > 0 ? mtR : tR, dy, shift_l(Lp));
+        F[a] = vfma(P0[a], cR[EX(a) + 1], in);
       } else {
-        const Real Lp = P0[a] * cL[EX(a) + 1];
-        F[a] = P0[a] * cR[EX(a) + 1] + __shfl_up_sync(kFull, Lp, 1);
+        F[a] = vfma(P0[a], cR[EX(a) + 1], shift_l(PcL));
       }
     }
     if (!INT && (touchW || touchE)) { // warp-uniform test first
-      if (i == 0 || i == nx) {
-        const int side = i == 0 ? 0 : 1;
-        face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, k.rho0, F);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (col[c] == 0 || col[c] == nx) {
+          const int side = col[c] == 0 ? 0 : 1;
+          Real s[9];
+          get(F, c, s);
+          face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, comp(k.rho0, 0), s);
+          put(F, c, s);
+        }
       }
     }
-    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, q_face, Real(WGT(1)), Real(WGT(5)));
+    if constexpr (DUG) dugks_face<Real, 0>(F, k.rho0, q_face);
   }
 
-  // Flux values of the y-face kf (between rows kf-1 and kf) at this column;
-  // Pl = phi of row kf-1, Pu = phi of row kf.
+  // Flux values of the y-face kf (between rows kf-1 and kf) at this lane's
+  // columns; Pl = phi of row kf-1, Pu = phi of row kf.
   template <bool INT>
-  __device__ __forceinline__ void yface(int kf, Real th, Real s, const Real (&Pl)[9],
-                                        const Real (&Pu)[9], Real (&F)[9]) {
+  __device__ __forceinline__ void yface(int kf, Real th, Real s, const V (&Pl)[9], const V (&Pu)[9],
+                                        V (&F)[9]) {
     const Real a0 = Real(1) - th, b0 = th;
+    const V va0 = V(a0), vb0 = V(b0), ap = V(a0 + s), bm = V(b0 - s), am = V(a0 - s), bp = V(b0 + s);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      if (!needy<SCHEME>(a)) continue;
-      Real B = a0 * Pl[a] + b0 * Pu[a];
-      Real own;
+      if (!needy<SCHEME>(a)) {
+        F[a] = V(Real(0));
+        continue;
+      }
+      V B = V(Real(0)), own;
+      if (EY(a) == 0 || EX(a) != 0) B = vfma(va0, Pl[a], vb0 * Pu[a]);
       if (EY(a) == 0)
         own = B;
       else if (EY(a) > 0)
-        own = (a0 + s) * Pl[a] + (b0 - s) * Pu[a];
+        own = vfma(ap, Pl[a], bm * Pu[a]);
       else
-        own = (a0 - s) * Pl[a] + (b0 + s) * Pu[a];
-      if (EX(a) != 0) {
-        Real Bn = __shfl_down_sync(kFull, B, 1);
-        Real Bs = __shfl_up_sync(kFull, B, 1);
-        own -= Real(EX(a)) * txc * (Bn - Bs);
-      }
+        own = vfma(am, Pl[a], bp * Pu[a]);
+      if (EX(a) != 0) own = vfma(EX(a) > 0 ? ntxc : txc, shift_r(B) - shift_l(B), own);
       F[a] = own;
     }
     if (!INT && !per_y && (kf == 0 || kf == ny)) {
       const int side = kf == 0 ? 2 : 3;
-      face_bc<Real>(A.seg[side][side == 2 ? segS : segN], 0, side == 2 ? -1 : 1, k.rho0, F);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        Real sv[9];
+        get(F, c, sv);
+        face_bc<Real>(A.seg[side][side == 2 ? segS[c] : segN[c]], 0, side == 2 ? -1 : 1,
+                      comp(k.rho0, 0), sv);
+        put(F, c, sv);
+      }
     }
-    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, q_face, Real(WGT(1)), Real(WGT(5)));
+    if constexpr (DUG) dugks_face<Real, 1>(F, k.rho0, q_face);
   }
 
-  __device__ __forceinline__ void store_row(int j, const Real (&v)[9]) {
+  template <bool INT> __device__ __forceinline__ void store_row(int j, const V (&v)[9]) {
     // element offsets fit in 32 bits: buffers are limited to 2^31 elements
-    const unsigned off = (unsigned)j * pitch + (unsigned)min(max(i, 0), nx - 1);
+    if (INT) {
+      const unsigned off = (unsigned)j * pitch + (unsigned)c0;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const Real x = encode<ST, Real>(v[a], a, k);
-      st_pred(fout + (off + a * plane), x, out_lane);
-    }
-  }
-
-  // One row of the finite-volume update.  DUGKS needs f_tilde^+ of the cell,
-  // recomputed from the staged values d and phi = f_bar^+ as
-  // f_tilde^+ = (4 phi - d) / 3 = phi + (phi - d) / 3 (the two transforms of
-  // Sec 2.2 combined; the increment form keeps equilibrium exact).
-  template <bool INT>
-  __device__ __forceinline__ void update_fv(int j, Real cyu, uint32_t stage, const Real (&Pb)[9],
-                                            const Real (&FW)[9], const Real (&FS)[9],
-                                            const Real (&FN)[9]) {
-    Real v[9];
-    if constexpr (DUG) {
-      Real d[9];
-      read_row<INT>(stage, d);
-#pragma unroll
-      for (int a = 0; a < 9; ++a) v[a] = Pb[a] + (Pb[a] - d[a]) * Real(1.0 / 3.0);
+      for (int a = 0; a < 9; ++a) st_lane(fout + (off + a * plane), encode<ST>(v[a], a, k), out_lane);
     } else {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) v[a] = Pb[a];
-    }
+      for (int c = 0; c < NC; ++c) {
+        const unsigned off = (unsigned)j * pitch + (unsigned)min(max(col[c], 0), nx - 1);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      if (EX(a) != 0) {
-        Real FE = __shfl_down_sync(kFull, FW[a], 1);
-        v[a] -= Real(EX(a)) * cxu * (FE - FW[a]);
+        for (int a = 0; a < 9; ++a) st_pred(fout + (off + a * plane), comp(encode<ST>(v[a], a, k), c), outc[c]);
       }
-      if (EY(a) != 0) v[a] -= Real(EY(a)) * cyu * (FN[a] - FS[a]);
     }
-    store_row(j, v);
-  }
-
-  // One row of the Lax-Wendroff stencil (Eqs. bkgfd, central_schemes).
-  __device__ __forceinline__ void update_fd(int j, const Real (&Pm)[9], const Real (&P0)[9],
-                                            const Real (&Pp)[9]) {
-    Real v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const int ex = EX(a), ey = EY(a);
-      // weights C[di][dj] of phi(i+di, j+dj): centre 1 - nx^2 - ny^2;
-      // (+-1,0): -+nx/2 + nx^2/2; (0,+-1): -+ny/2 + ny^2/2; corners +-nx ny/4
-      const Real cxm = ex ? (Real(ex) * kx1 + kx2) : Real(0); // di = -1
-      const Real cxp = ex ? (kx2 - Real(ex) * kx1) : Real(0); // di = +1
-      const Real cym = ey ? (Real(ey) * ky1 + ky2) : Real(0);
-      const Real cyp = ey ? (ky2 - Real(ey) * ky1) : Real(0);
-      const Real cc = Real(1) - (ex ? Real(2) * kx2 : Real(0)) - (ey ? Real(2) * ky2 : Real(0));
-      Real M = cc * P0[a];
-      if (ey) M += cym * Pm[a] + cyp * Pp[a];
-      if (ex) {
-        // column parts for the neighbours: this column is di = +1 for the
-        // left neighbour and di = -1 for the right one
-        Real forL = cxp * P0[a], forR = cxm * P0[a];
-        if (ey) {
-          const Real kc = Real(ex * ey) * kxy;
-          forL += kc * (Pp[a] - Pm[a]);
-          forR -= kc * (Pp[a] - Pm[a]);
-        }
-        M += __shfl_down_sync(kFull, forL, 1) + __shfl_up_sync(kFull, forR, 1);
-      }
-      v[a] = M;
-    }
-    store_row(j, v);
   }
 
   // Logical row L (-1 .. ny) is stored (periodic wrap) unless it is a ghost row.
@@ -874,14 +1018,52 @@ template <int SCHEME, int ST> struct Strip {
     t.jb = jb;
   }
 
-  // One full row j: phi of row j+1 into Pc (unless have_next), faces, update.
-  // Pa, Pb, Pc = phi of rows j-1, j, j+1; stj / stn = stages holding rows j
-  // and j+1 (stj is released at the end of the row).  INT: the strip touches
-  // no boundary (all its columns and rows j0-1 .. jend are inner cells), so
-  // the ghost, wrap and boundary-face code is compiled out.
+  // One row of the Lax-Wendroff stencil (Eqs. bkgfd, central_schemes).
   template <bool INT>
-  __device__ __forceinline__ void row(int j, int jend, bool have_next, RowTab &rt, Real (&Pa)[9],
-                                      Real (&Pb)[9], Real (&Pc)[9], Real (&FS)[9], uint32_t &stj,
+  __device__ __forceinline__ void update_fd(int j, const V (&Pm)[9], const V (&P0)[9], const V (&Pp)[9]) {
+    V v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const int ex = EX(a), ey = EY(a);
+      // weights C[di][dj] of phi(i+di, j+dj): centre 1 - nx^2 - ny^2;
+      // (+-1,0): -+nx/2 + nx^2/2; (0,+-1): -+ny/2 + ny^2/2; corners +-nx ny/4
+      const Real cxm = ex ? (Real(ex) * kx1 + kx2) : Real(0); // di = -1
+      const Real cxp = ex ? (kx2 - Real(ex) * kx1) : Real(0); // di = +1
+      const Real cym = ey ? (Real(ey) * ky1 + ky2) : Real(0);
+      const Real cyp = ey ? (ky2 - Real(ey) * ky1) : Real(0);
+      const Real cc = Real(1) - (ex ? Real(2) * kx2 : Real(0)) - (ey ? Real(2) * ky2 : Real(0));
+      V M = V(cc) * P0[a];
+      if (ey) M = vfma(V(cym), Pm[a], vfma(V(cyp), Pp[a], M));
+      if (ex) {
+        // column parts for the neighbours: this column is di = +1 for the
+        // left neighbour and di = -1 for the right one
+        V forL = V(cxp) * P0[a], forR = V(cxm) * P0[a];
+        if (ey) {
+          const Real kc = Real(ex * ey) * kxy;
+          const V dyv = Pp[a] - Pm[a];
+          forL = vfma(V(kc), dyv, forL);
+          forR = vfma(V(-kc), dyv, forR);
+        }
+        M = M + (shift_r(forL) + shift_l(forR));
+      }
+      v[a] = M;
+    }
+    store_row<INT>(j, v);
+  }
+
+  // One full row j: phi of row j+1 into Pc (unless have_next), the faces and
+  // the finite-volume update (Eqs. eq_update, lwfv, bkg_fv), accumulated
+  // face by face.  DUGKS needs f_tilde^+ of the cell, recomputed from the
+  // staged values d and phi = f_bar^+ as f_tilde^+ = (4 phi - d) / 3 =
+  // phi + (phi - d) / 3 (the two transforms of Sec 2.2 combined; the
+  // increment form keeps equilibrium exact).  Pa, Pb, Pc = phi of rows j-1,
+  // j, j+1; stj / stn = stages holding rows j and j+1 (stj is released at
+  // the end of the row).  INT: the strip touches no boundary (all its
+  // columns and rows j0-1 .. jend are inner cells), so the ghost, wrap and
+  // boundary-face code is compiled out.
+  template <bool INT>
+  __device__ __forceinline__ void row(int j, int jend, bool have_next, RowTab &rt, V (&Pa)[9],
+                                      V (&Pb)[9], V (&Pc)[9], V (&FS)[9], uint32_t &stj,
                                       uint32_t &stn) {
     if (j - rt.jb >= 32) load_rows(rt, j);
     const int q = j - rt.jb;
@@ -897,14 +1079,38 @@ template <int SCHEME, int ST> struct Strip {
       }
     }
     if constexpr (FD) {
-      update_fd(j, Pa, Pb, Pc);
+      update_fd<INT>(j, Pa, Pb, Pc);
     } else {
-      Real FW[9], FN[9];
-      xface<INT>(j, tyc, Pa, Pb, Pc, FW);
-      yface<INT>(j + 1, th, sl, Pb, Pc, FN);
-      update_fv<INT>(j, cyu, stj, Pb, FW, FS, FN);
+      V v[9];
+      if constexpr (DUG) {
+        V d[9];
+        read_row<INT>(stj, d);
 #pragma unroll
-      for (int a = 0; a < 9; ++a) FS[a] = FN[a];
+        for (int a = 0; a < 9; ++a) v[a] = vfma(Pb[a] - d[a], V(Real(1.0 / 3.0)), Pb[a]);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = Pb[a];
+      }
+      {
+        V F[9];
+        xface<INT>(j, tyc, Pa, Pb, Pc, F);
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+          if (EX(a) != 0) v[a] = vfma(EX(a) > 0 ? ncxu : cxu, shift_r(F[a]) - F[a], v[a]);
+      }
+      {
+        V F[9];
+        yface<INT>(j + 1, th, sl, Pb, Pc, F);
+        const V cy = V(cyu), ncy = V(-cyu);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          if (EY(a) != 0) {
+            v[a] = vfma(EY(a) > 0 ? ncy : cy, F[a] - FS[a], v[a]);
+            FS[a] = F[a];
+          }
+        }
+      }
+      store_row<INT>(j, v);
     }
     release<INT>();
     stj = stn;
@@ -920,7 +1126,7 @@ template <int SCHEME, int ST> struct Strip {
     while (nissued < nfetch && nissued < P::NS) issue<INT>();
     RowTab rt;
     load_rows(rt, j0);
-    Real P0[9], P1[9], P2[9], FS[9];
+    V P0[9], P1[9], P2[9], FS[9];
     uint32_t stj, stn = 0;
     bool have_next = false;
     if (ghost_bottom) {
@@ -938,7 +1144,9 @@ template <int SCHEME, int ST> struct Strip {
     }
     if constexpr (!FD)
       yface<INT>(j0, ((const Real *)A.yfth)[j0 + 1], ((const Real *)A.yfs)[j0 + 1], P0, P1, FS);
-    if constexpr (INT && (DUG ? DVBE_DUGKS_UNROLL : DVBE_BKG_UNROLL)) {
+    constexpr bool UNROLL = NC == 1 ? (DUG ? DVBE_DUGKS_UNROLL : DVBE_BKG_UNROLL)
+                                    : (DUG ? DVBE_PAIR_DUGKS_UNROLL : DVBE_PAIR_BKG_UNROLL);
+    if constexpr (INT && UNROLL) {
       // unrolled by three so that the phi rows rotate by renaming
       int j = j0;
       while (true) {
@@ -968,8 +1176,8 @@ template <int SCHEME, int ST> struct Strip {
     setup(sx);
     const int j0 = sy * A.H;
     const int jend = min(j0 + A.H, ny);
-    // inner strip: its 32 columns and the rows j0-1 .. jend all exist
-    const bool inner = i0 >= 1 && i0 + kStripCols <= nx - 1 && j0 >= 1 && jend <= ny - 1;
+    // inner strip: its columns i0 - 1 .. i0 + COLS and the rows j0-1 .. jend all exist
+    const bool inner = i0 >= 1 && i0 + COLS <= nx - 1 && j0 >= 1 && jend <= ny - 1;
     if (inner)
       run_t<true>(j0, jend);
     else
@@ -997,11 +1205,18 @@ template <int SCHEME, int ST> struct Strip {
   }
 };
 
+// Blocks of 256 threads per SM the step kernel is compiled for.
+template <int SCHEME, int ST> constexpr int min_blocks() {
+  return LaneT<typename StoreT<ST>::Real>::NC == 2
+             ? DVBE_PAIR_MINB
+             : (SCHEME == SC_DUGKS ? DVBE_DUGKS_MINB : DVBE_BKG_MINB);
+}
+
 template <int SCHEME, int ST>
-__global__ void __launch_bounds__(256, SCHEME == SC_DUGKS ? DVBE_DUGKS_MINB : DVBE_BKG_MINB)
+__global__ void __launch_bounds__(256, min_blocks<SCHEME, ST>())
     k_step(const __grid_constant__ CaseArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
-  using P = Pipe<(int)sizeof(typename StoreT<ST>::T)>;
+  using P = typename Strip<SCHEME, ST>::P;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1026,7 +1241,7 @@ __global__ void __launch_bounds__(256, 1)
     k_step_batch(const CaseArgs *__restrict__ cases, const long long *__restrict__ prefix,
                  int ncases, long long nitems, unsigned long long *queue) {
   extern __shared__ __align__(128) unsigned char smem[];
-  using P = Pipe<(int)sizeof(typename StoreT<ST>::T)>;
+  using P = typename Strip<SCHEME, ST>::P;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const uint32_t sb = smem_u32(smem) + wib * P::WARPB;
@@ -1078,7 +1293,7 @@ __global__ void __launch_bounds__(256, 1)
 } // namespace dev
 
 template <int ST> constexpr int warp_smem() {
-  return dev::Pipe<(int)sizeof(typename dev::StoreT<ST>::T)>::WARPB;
+  return dev::Strip<SC_DUGKS, ST>::P::WARPB;
 }
 
 template <typename K> cudaError_t allow_smem(K kern, int bytes) {
