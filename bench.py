@@ -354,13 +354,16 @@ def main():
     s.close()
     acc = accuracy(dv, a.scheme, a.precision) if rank == 0 and a.precision != "f64" else None
 
+    fbytes = BYTES_PER_CELL[a.precision] // 2 * cells
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision], "data": "synthetic",
             "config": dict(workload_config(a), **{
-                       "l2": "inputs larger than L2 (two 604 MB f_tilde buffers), no flush",
+                       "l2": (f"inputs larger than L2 (two {fbytes / 1e6:.0f} MB f_tilde buffers), no flush"
+                              if fbytes > 129e6 else
+                              f"f_tilde buffers of {fbytes / 1e6:.0f} MB fit in L2: not a bench configuration"),
                        "parallelism": f"replicas x{world}", "launch": launch,
                        "autotune_ms_per_step": tuned_ms}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
