@@ -132,6 +132,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(t, world, device):
+    """Slowest rank's time: each rank runs its own replica of the workload
+    (no collective on the data path), so the whole job takes the max."""
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_mlups(world, cells, steps, t):
+    """Whole-job throughput: the cell updates of all ranks over the slowest rank's time."""
+    return world * cells * steps / t / 1e6
+
+
 def time_steps(dv, s, stream, torch, K):
     """K steps on the solver's stream bracketed by CUDA events on that stream."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -301,11 +318,8 @@ def main():
     t, launches = time_steps(dv, s, stream, torch, a.steps)
     barrier()
     ck = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * cells * a.steps / t / 1e6
+    t = max_over_ranks(t, world, "cuda")
+    value = job_mlups(world, cells, a.steps, t)
     per_launch = t / a.steps
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL[a.precision] * cells / per_launch / 1e9
@@ -322,9 +336,9 @@ def main():
     s.step(a.steps)
     r, u, v = s.moments()
     barrier()
-    te = time.perf_counter() - t0
+    te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     outs[0][...] = r
-    e2e = {"value": world * cells * a.steps / te / 1e6, "unit": "MLUPS",
+    e2e = {"value": job_mlups(world, cells, a.steps, te), "unit": "MLUPS",
            "h2d_bytes_per_step": pin.nbytes / a.steps, "d2h_bytes_per_step": 3 * cells * 8 / a.steps,
            "note": "init_f from pinned host f_tilde (float64), the steps, get_moments to host"}
 
