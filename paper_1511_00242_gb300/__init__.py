@@ -439,7 +439,7 @@ class Solver:
 class Batch:
     """Many independent cases stepped by one persistent launch per scheme."""
 
-    def __init__(self, cases, precision="f32"):
+    def __init__(self, cases, precision="f32", allow_cfl_ge_1=False):
         self.cases = cases
         meshes, keeps = [], []
         arr = (dvbe_params * len(cases))()
@@ -447,7 +447,7 @@ class Batch:
             for k, case in enumerate(cases):
                 m = dvbe_mesh_create(case["xf"], case["yf"])
                 meshes.append(m)
-                p, keep = make_params(case, m, precision)
+                p, keep = make_params(case, m, precision, allow_cfl_ge_1=allow_cfl_ge_1)
                 keeps.append(keep)
                 arr[k] = p
             h = ctypes.c_void_p()

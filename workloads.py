@@ -303,3 +303,18 @@ def batched_cases(ncases: int = 512, seed: int = 1511, side_max: int = 512,
         case["cfl"] = cfl
         out.append((case, fields))
     return out
+
+
+def cavity_at_ratio(point, ratio: float):
+    """Lid-driven cavity for the stability map (Sec 3.2, Fig. cavity_stab):
+    point = (scheme, n, cfl); lid U = 0.1 c, fluid at rest (impulsive start),
+    n x n uniform mesh, dt from the CFL number and tau = dt / ratio (so
+    nu = tau RT and Re = U L / nu follow from the ratio)."""
+    scheme, n, cfl = point
+    xf = uniform_faces(n, 0.0, 1.0)
+    dt = cfl_dt(xf, xf, cfl)
+    tau = dt / ratio
+    Re = 0.1 * 1.0 / (tau * RT_LATTICE)
+    case, fields = cavity(n, Re=Re, U=0.1, cfl=cfl, scheme=scheme)
+    case["U"] = 0.1
+    return case, fields
