@@ -58,6 +58,40 @@ def test_table1_on_gpu(dv, scheme):
         assert 1.8 < math.log2(errs[a] / errs[b]) < 2.3
 
 
+def test_time_step_sweep_n64(dv):
+    """Sec 3.1, Fig. tv_dtErr: N = 64, tau fixed, dt/tau = 5 .. 50.  The error
+    at t_c grows almost linearly with dt once the time error dominates, the
+    DUGKS error stays below BKG's at every dt, and both schemes blow up at
+    dt/tau = 100, where the CFL number (dt |xi|_max / dx = 1.57) exceeds 1."""
+    errs = {}
+    for scheme in ("dugks", "bkg"):
+        for ratio in (5.0, 10.0, 20.0, 50.0):
+            case, fields, d, tc = W.taylor_green_paper(64, scheme, dt_over_tau=ratio)
+            steps = int(round(tc / case["dt"]))
+            with dv.Solver(case, precision="f64") as s:
+                s.set_launch(strip_rows=16, warps_per_block=2, graph_chunk=1000)
+                s.init_chapman_enskog(*fields, d)
+                s.step(steps)
+                errs[(scheme, ratio)] = s.l2_error_u(*W.taylor_green_paper_analytic(case, steps * case["dt"]))
+            print(f"dt sweep {scheme} dt/tau={ratio:g}: E_u(t_c)={errs[(scheme, ratio)]:.4e}")
+    for scheme in ("dugks", "bkg"):
+        e = [errs[(scheme, r)] for r in (5.0, 10.0, 20.0, 50.0)]
+        assert all(a < b for a, b in zip(e, e[1:]))
+        slope = math.log(e[3] / e[2]) / math.log(50.0 / 20.0)
+        assert 0.7 < slope < 1.3, slope
+    for ratio in (5.0, 10.0, 20.0, 50.0):
+        assert errs[("dugks", ratio)] < errs[("bkg", ratio)]
+    for scheme in ("dugks", "bkg"):
+        case, fields, d, tc = W.taylor_green_paper(64, scheme, dt_over_tau=100.0)
+        cfl = case["dt"] * math.sqrt(6.0 * case["RT"]) / (1.0 / 64)
+        assert cfl > 1.0
+        with dv.Solver(case, precision="f64", allow_cfl_ge_1=True) as s:
+            s.init_chapman_enskog(*fields, d)
+            with pytest.raises(dv.DvbeError) as e:
+                s.step(int(round(tc / case["dt"])))
+            assert e.value.status == dv.DVBE_ERR_DIVERGED
+
+
 def test_dugks_more_accurate_than_bkg_at_n32(dv):
     """Sec 3.1: DUGKS errors below BKG's on the same mesh."""
     out = {}

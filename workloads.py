@@ -102,9 +102,10 @@ def taylor_green_box_analytic(case, t: float):
     return -u0 * np.cos(x) * np.sin(y) * d, u0 * np.sin(x) * np.cos(y) * d
 
 
-def taylor_green_paper(n: int, scheme: str = "dugks"):
+def taylor_green_paper(n: int, scheme: str = "dugks", dt_over_tau: float = 2.0):
     """The set-up of Sec 3.1: unit box, U0 = 1e-2/sqrt(3), nu = 1e-4/sqrt(3),
-    dt = 2 tau, Chapman-Enskog initial state from the analytic solution.
+    dt = 2 tau (Table tab:tv_Nerr; other dt/tau for the time-step sweep of
+    Fig. tv_dtErr), Chapman-Enskog initial state from the analytic solution.
 
     Returns (case, fields, derivs, t_c) with derivs = (rho_t, ux_t, uy_t, rho_x,
     ux_x, uy_x, rho_y, ux_y, uy_y) of the analytic solution at t = 0 and
@@ -113,7 +114,7 @@ def taylor_green_paper(n: int, scheme: str = "dugks"):
     U0 = 1e-2 / math.sqrt(3.0)
     nu = 1e-4 / math.sqrt(3.0)
     tau = nu / RT_LATTICE
-    dt = 2.0 * tau
+    dt = dt_over_tau * tau
     xf = uniform_faces(n, 0.0, 1.0)
     yf = uniform_faces(n, 0.0, 1.0)
     case = dict(nx=n, ny=n, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme,
