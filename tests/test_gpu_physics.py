@@ -133,6 +133,60 @@ def test_cavity_reaches_steady_state(dv, scheme):
     assert uc[-1] > 0 and uc.min() < -0.02
 
 
+def _centerlines(u, v):
+    """u on the vertical centre line and v on the horizontal one (cell-centre
+    averages of the two columns / rows next to x = 0.5 / y = 0.5)."""
+    n = u.shape[0]
+    return 0.5 * (u[:, n // 2 - 1] + u[:, n // 2]), 0.5 * (v[n // 2 - 1, :] + v[n // 2, :])
+
+
+def _coarsen(a):
+    """Values of a 2n mesh at the n mesh's cell centres along a line (pairs averaged)."""
+    return 0.5 * (a[0::2] + a[1::2])
+
+
+def test_bkg_cfl_sweep_cavity_re5000(dv):
+    """Sec 3.2, Fig. cavity_cfl: lid-driven cavity at Re = 5000 on 128^2.  The
+    BKG centre-line errors decrease with the CFL number, and even at CFL 0.1
+    they stay above those of DUGKS on the same mesh.  The paper measures
+    against Ghia's data, which are not available here; the reference is DUGKS
+    on 256^2.  All runs go to t = 100 L/U, FP32 deviation storage."""
+    T = 1000.0
+
+    def run(n, scheme, cfl):
+        case, fields = W.cavity(n, Re=5000, cfl=cfl, scheme=scheme)
+        with dv.Solver(case, precision="f32_dev") as s:
+            s.set_launch(strip_rows=16, graph_chunk=1000)
+            s.init_equilibrium(*fields)
+            s.step(int(round(T / case["dt"])))
+            s.residual()
+            s.step(1000)
+            r = s.residual()
+            _, u, v = s.moments()
+        return _centerlines(u, v), r
+
+    (ur, vr), rr = run(256, "dugks", 0.5)
+    ref = (_coarsen(ur), _coarsen(vr))
+
+    def err(lines):
+        return float(np.sqrt((np.sum((lines[0] - ref[0]) ** 2) + np.sum((lines[1] - ref[1]) ** 2))
+                             / (np.sum(ref[0] ** 2) + np.sum(ref[1] ** 2))))
+
+    errs = {}
+    for cfl in (0.1, 0.3, 0.5, 0.7):
+        lines, r = run(128, "bkg", cfl)
+        errs[("bkg", cfl)] = err(lines)
+        print(f"cavity Re5000 128^2 BKG CFL {cfl}: centre-line error vs DUGKS 256^2 = "
+              f"{errs[('bkg', cfl)]:.3e} (residual {r:.1e})")
+    lines, r = run(128, "dugks", 0.5)
+    errs[("dugks", 0.5)] = err(lines)
+    print(f"cavity Re5000 128^2 DUGKS CFL 0.5: {errs[('dugks', 0.5)]:.3e} (residual {r:.1e}; "
+          f"reference residual {rr:.1e})")
+    e = [errs[("bkg", c)] for c in (0.1, 0.3, 0.5, 0.7)]
+    assert all(a < b for a, b in zip(e, e[1:]))
+    assert errs[("dugks", 0.5)] < errs[("bkg", 0.1)]
+
+
 def test_precision_modes_against_fp64_and_analytic(dv):
     """Taylor-Green 256^2, dt/tau = 10, to 10% decay (21k steps): error of
     each storage mode against the FP64 path (E_p) and of the FP64 path against
