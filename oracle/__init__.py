@@ -6,7 +6,7 @@ product library never loads it, and it shares no code with the CUDA path.
 
 Problems are described as plain data (see ``workloads.py``):
 
-    case = dict(nx=, ny=, xf=, yf=, RT=, tau=, dt=, scheme="dugks"|"bkg",
+    case = dict(nx=, ny=, xf=, yf=, RT=, tau=, dt=, scheme="dugks"|"bkg"|"cfree_upwind"|"cfree_central",
                 bc=[W, E, S, N])      # each side: list of (kind, s0, s1, rho, ux, uy)
 
 with kind one of "periodic", "wall", "diffuse", "inflow", "outflow",
@@ -26,7 +26,7 @@ _HDR = os.path.join(_HERE, "dvbe_oracle.h")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5}
-SCHEMES = {"dugks": 0, "bkg": 1}
+SCHEMES = {"dugks": 0, "bkg": 1, "cfree_upwind": 2, "cfree_central": 3}
 
 
 def build(force: bool = False) -> str:

@@ -4,10 +4,12 @@
  *
  * The step is written in the paper's order with explicit arrays:
  *   1. cell moments and equilibrium               (Sec 2.1, Eq. macro_var)
- *   2. phi = f_bar^+ (DUGKS) or f_tilde^+ (BKG)   (Eqs. eq_trans_2, bkg_collision)
+ *   2. phi = f_bar^+ (DUGKS), f_tilde^+ (BKG) or the cell f^n (collision-free
+ *      faces of Eqs. cfd1 / cfd2)               (Eqs. eq_trans_2, bkg_collision)
  *   3. ghost layer of phi                         (Sec 2.5)
  *   4. face values phi(x_b - h xi) by linear reconstruction
- *                                                 (Eqs. eq_char, bkg_fb, f_left)
+ *                                                 (Eqs. eq_char, bkg_fb, f_left);
+ *      phi(x_b) for the central collision-free face (Eq. cfd1)
  *   5. wall / inflow treatment at boundary faces  (Sec 2.5)
  *   6. DUGKS: face moments, back-transform to f   (Sec 2.2 after Eq. eq_char)
  *   7. flux and update                            (Eqs. eq_update, eq_flux, lwfv, bkg_fv)
@@ -228,7 +230,7 @@ static int geom_build(const orc_problem *p, geom *g) {
   memset(g, 0, sizeof(*g));
   if (!p || p->nx < 2 || p->ny < 2 || !p->xf || !p->yf) return ORC_EINVAL;
   if (!(p->RT > 0.0) || !(p->tau > 0.0) || !(p->dt > 0.0)) return ORC_EINVAL;
-  if (p->scheme != ORC_DUGKS && p->scheme != ORC_BKG) return ORC_EINVAL;
+  if (p->scheme < ORC_DUGKS || p->scheme > ORC_CFREE_CENTRAL) return ORC_EINVAL;
   for (int i = 0; i < p->nx; ++i)
     if (!(p->xf[i + 1] > p->xf[i])) return ORC_EINVAL;
   for (int j = 0; j < p->ny; ++j)
@@ -511,8 +513,10 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
         double phi;
         if (p->scheme == ORC_DUGKS)
           phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);
-        else
+        else if (p->scheme == ORC_BKG)
           phi = tplus;
+        else /* collision-free faces: the cell f^n itself */
+          phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);
         TP[a * n + k] = tplus;
         P[a * plane + PIDX(g, i, j)] = phi;
       }
@@ -521,10 +525,12 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
   /* 3: ghost layer */
   fill_ghosts(v, g, P);
 
-  /* 4-6: x-faces i = 0..nx, rows 0..ny-1 */
+  /* 4-6: x-faces i = 0..nx, rows 0..ny-1; the central collision-free face
+     takes phi at x_b itself (no shift along the characteristic) */
+  const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;
   for (int j = 0; j < ny; ++j) {
     for (int i = 0; i <= nx; ++i) {
-      recon_xface(v, g, P, i, j, h, val);
+      recon_xface(v, g, P, i, j, hs, val);
       if (!g->per_x && i == 0) face_bc(v, g->segW[j], -1.0, 0.0, val);
       if (!g->per_x && i == nx) face_bc(v, g->segE[j], 1.0, 0.0, val);
       face_to_f(v, p, val);
@@ -534,7 +540,7 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
   /* y-faces j = 0..ny, columns 0..nx-1 */
   for (int j = 0; j <= ny; ++j) {
     for (int i = 0; i < nx; ++i) {
-      recon_yface(v, g, P, i, j, h, val);
+      recon_yface(v, g, P, i, j, hs, val);
       if (!g->per_y && j == 0) face_bc(v, g->segS[i], 0.0, -1.0, val);
       if (!g->per_y && j == ny) face_bc(v, g->segN[i], 0.0, 1.0, val);
       face_to_f(v, p, val);
@@ -781,6 +787,7 @@ static int implicit_bkg_once(const orc_problem *p, const vset *v, const geom *g,
 
 int orc_step_implicit(const orc_problem *p, double *f, long long nsteps) {
   if (!f || nsteps < 0) return ORC_EINVAL;
+  if (!p || (p->scheme != ORC_DUGKS && p->scheme != ORC_BKG)) return ORC_EINVAL;
   geom g;
   int rc = geom_build(p, &g);
   if (rc) return rc;

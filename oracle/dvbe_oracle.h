@@ -33,7 +33,11 @@
 extern "C" {
 #endif
 
-enum { ORC_DUGKS = 0, ORC_BKG = 1 };
+/* DUGKS (Sec 2.2), BKG (Sec 2.3), and the two collision-free face values
+ * of Sec 2.4: the upwind value f^n(x_b - h xi) (Eq. cfd2) and the central
+ * value f^n(x_b) (Eq. cfd1), both from the cell f^n with no collision term
+ * in the flux. */
+enum { ORC_DUGKS = 0, ORC_BKG = 1, ORC_CFREE_UPWIND = 2, ORC_CFREE_CENTRAL = 3 };
 
 enum {
   ORC_BC_PERIODIC = 0,
@@ -63,7 +67,7 @@ typedef struct {
   const double *xf; /* nx+1 x-face coordinates, strictly increasing */
   const double *yf; /* ny+1 y-face coordinates, strictly increasing */
   double RT, tau, dt;
-  int scheme;       /* ORC_DUGKS or ORC_BKG */
+  int scheme;       /* ORC_DUGKS, ORC_BKG, ORC_CFREE_UPWIND or ORC_CFREE_CENTRAL */
   int nbc[4];       /* segments per side, W E S N */
   const orc_bc_segment *bc[4];
 } orc_problem;

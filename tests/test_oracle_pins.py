@@ -90,7 +90,10 @@ def test_dt_from_cfl_and_faces():
 
 # ---------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+ALL_SCHEMES = ["dugks", "bkg", "cfree_upwind", "cfree_central"]
+
+
+@pytest.mark.parametrize("scheme", ALL_SCHEMES)
 @pytest.mark.parametrize("stretched", [False, True])
 def test_uniform_flow_is_a_fixed_point(scheme, stretched):
     """A uniform equilibrium stays put: transform coefficients sum to one and
@@ -103,7 +106,7 @@ def test_uniform_flow_is_a_fixed_point(scheme, stretched):
     assert np.max(np.abs(f - f0)) < 2e-16 * 20
 
 
-@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("scheme", ALL_SCHEMES)
 def test_conservation_periodic(scheme):
     """Eq. eq:convervation + flux telescoping: mass and momentum are exact on a
     periodic mesh, stretched in x."""
@@ -246,6 +249,63 @@ def test_linear_fields_advect_exactly_on_random_mesh(scheme):
     assert np.max(np.abs(f1[inner] - ex[inner])) < 1e-16
 
 
+# ------------------------------------------- collision-free faces (Sec 2.4)
+
+@pytest.mark.parametrize("scheme", ALL_SCHEMES)
+def test_quadratic_cell_averages_collisionless(scheme):
+    """Collisions off (tau = 1e30), uniform mesh, f = w (1 + g x^2) as cell
+    averages (x_i^2 + dx^2/12).  Exact advection by xi dt changes a cell
+    average by g (-2 xi_x dt x_i + xi_x^2 dt^2).  Faces taken at x_b - h xi
+    (DUGKS, BKG and the upwind face of Eq. cfd2) reproduce it exactly; the
+    central face of Eq. cfd1 (at x_b) misses exactly g w xi_x^2 dt^2."""
+    n = 16
+    case = periodic_case(n, 6, scheme, tau=1e30)
+    dt = case["dt"]
+    xi, w, _ = O.d2q9(RT)
+    dx = 1.0 / n
+    x, _ = np.meshgrid(W.centres(case["xf"]), W.centres(case["yf"]))
+    g = 1e-2
+    f0 = np.array([w[a] * (1 + g * (x * x + dx * dx / 12)) for a in range(9)])
+    f1 = O.step(case, f0, 1)
+    ex = np.array([w[a] * (1 + g * (x * x + dx * dx / 12 - 2 * xi[a, 0] * dt * x + (xi[a, 0] * dt) ** 2))
+                   for a in range(9)])
+    if scheme == "cfree_central":
+        ex -= np.array([w[a] * g * (xi[a, 0] * dt) ** 2 * np.ones_like(x) for a in range(9)])
+    inner = (slice(None), slice(None), slice(2, n - 2))
+    assert np.max(np.abs(f1[inner] - ex[inner])) < 1e-16
+
+
+def _feq_closed_form(rho, ux, uy):
+    """Eq. equilibrium for D2Q9 with RT = 1/3 (c = 1), written out here."""
+    e = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    wt = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    out = []
+    for (ex, ey), wa in zip(e, wt):
+        eu = ex * ux + ey * uy
+        out.append(wa * rho * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy)))
+    return np.array(out)
+
+
+def test_upwind_collision_free_face_identity():
+    """Eq. cfd2 with the cell f^n: the flux is linear in the reconstructed
+    variable, f^n = (f_tilde + f_tilde^+)/2 and BKG reconstructs f_tilde^+, so
+    one step obeys  U(f) = (B_0(f) - f)/2 + (B(f) + f_tilde^+)/2  with B the BKG
+    step at the same tau, B_0 the collisionless BKG step and f_tilde^+ =
+    ((2 tau - dt) f + 2 dt f_eq)/(2 tau + dt) from the closed forms."""
+    case = periodic_case(14, 10, "cfree_upwind", tau=0.004, xf=W.tanh_faces(14, 0.0, 1.0, 1.0))
+    (r, u, v), delta = W.random_state(case, 5, amp_neq=2e-3)
+    f = O.init_equilibrium(case, r, u, v) + delta
+    up = O.step(case, f, 1)
+    bkg = O.step(dict(case, scheme="bkg"), f, 1)
+    bkg0 = O.step(dict(case, scheme="bkg", tau=1e30), f, 1)
+    rho, ux, uy = O.moments(case, f)
+    tau, dt = case["tau"], case["dt"]
+    tplus = ((2 * tau - dt) * f + 2 * dt * _feq_closed_form(rho, ux, uy)) / (2 * tau + dt)
+    pred = 0.5 * (bkg0 - f) + 0.5 * (bkg + tplus)
+    assert np.max(np.abs(up - pred)) < 1e-14
+    assert np.max(np.abs(up - bkg)) > 1e-6  # the identity is not trivially satisfied
+
+
 # ---------------------------------------------------------------- walls / BCs
 
 @pytest.mark.parametrize("scheme", ["dugks", "bkg"])
@@ -371,6 +431,12 @@ MUTATIONS = {
     # bounce-back with the wrong sign of the wall term
     "bounce_sign": ("val[v->opp[a]] = orig[a] - 2.0 * v->w[a] * xu / v->cs2;",
                     "val[v->opp[a]] = orig[a] + 2.0 * v->w[a] * xu / v->cs2;"),
+    # the central collision-free face taken at the foot of the characteristic
+    "central_shift": ("const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;",
+                      "const double hs = h;"),
+    # the collision-free faces reconstructing f_tilde^+ instead of f^n
+    "cfree_phi": ("phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);",
+                  "phi = tplus;"),
     # transposed theta in the y-face blend
     "theta_swap": ("double value = (1.0 - th) * pl + th * pr;\n    double slope_n = (pr - pl) / (yr - yl);",
                    "double value = th * pl + (1.0 - th) * pr;\n    double slope_n = (pr - pl) / (yr - yl);"),
@@ -411,6 +477,8 @@ def _pins_with(so_path):
             "stretched_fp": lambda: test_uniform_flow_is_a_fixed_point("dugks", True),
             "stretched_order": lambda: test_stretched_mesh_advection_is_second_order("dugks"),
             "linear_exact": lambda: test_linear_fields_advect_exactly_on_random_mesh("dugks"),
+            "quadratic_central": lambda: test_quadratic_cell_averages_collisionless("cfree_central"),
+            "cfree_identity": lambda: test_upwind_collision_free_face_identity(),
         }
         for k, fn in checks.items():
             try:
