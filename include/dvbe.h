@@ -46,7 +46,18 @@ typedef enum {
   DVBE_ERR_UNSUPPORTED = 7  /* valid request this build does not provide     */
 } dvbe_status;
 
-typedef enum { DVBE_DUGKS = 0, DVBE_BKG = 1 } dvbe_scheme;
+/* DVBE_DUGKS: Sec 2.2.  DVBE_BKG: Sec 2.3.  The two collision-free face
+ * values that Sec 2.4 contrasts with them (Eqs. cfd2, cfd1): the cell f^n
+ * reconstructed at x_b - h xi (upwind) or at x_b (central) is the flux
+ * distribution itself, with no collision term; the update starts from
+ * f_tilde^+ as in the other schemes.  These two run on the single solver
+ * only (dvbe_batch_create rejects them). */
+typedef enum {
+  DVBE_DUGKS = 0,
+  DVBE_BKG = 1,
+  DVBE_CFREE_UPWIND = 2,
+  DVBE_CFREE_CENTRAL = 3
+} dvbe_scheme;
 
 /* Storage of f_tilde in device memory.  Arithmetic is FP64 for DVBE_F64 and
  * FP32 for every other mode.  *_DEV modes store d = (f_tilde - w_alpha rho0)/s_alpha;

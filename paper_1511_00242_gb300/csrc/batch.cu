@@ -143,6 +143,8 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
     st = build_problem(&cases[c], b->pb[c]);
     if (st == DVBE_OK && b->pb[c].kernel == SC_BKG_FD)
       st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs BKG in finite-volume form only");
+    if (st == DVBE_OK && b->pb[c].kernel == SC_CFREE)
+      st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs DUGKS and BKG only");
     if (st == DVBE_OK && c > 0 && b->pb[c].store != b->pb[0].store)
       st = fail(DVBE_ERR_INVALID_ARG, "all cases of a batch must share one precision");
     if (st == DVBE_OK) st = upload_problem(b->pb[c], b->dp[c], b->args[c], b->stream);

@@ -118,7 +118,7 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   if (!(p->RT > 0) || !(p->tau > 0) || !(p->dt > 0) || !std::isfinite(p->RT) ||
       !std::isfinite(p->dt) || std::isnan(p->tau))
     return fail(DVBE_ERR_INVALID_ARG, "RT, tau and dt must be positive and finite");
-  if (p->scheme != DVBE_DUGKS && p->scheme != DVBE_BKG)
+  if (p->scheme < DVBE_DUGKS || p->scheme > DVBE_CFREE_CENTRAL)
     return fail(DVBE_ERR_INVALID_ARG, "unknown scheme");
   if (p->precision < DVBE_F64 || p->precision > DVBE_BF16_DEV)
     return fail(DVBE_ERR_INVALID_ARG, "unknown precision");
@@ -166,7 +166,7 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
     return fail(DVBE_ERR_CFL, b);
   }
 
-  pb.kernel = p->scheme == DVBE_DUGKS ? SC_DUGKS : SC_BKG_FV;
+  pb.kernel = p->scheme == DVBE_DUGKS ? SC_DUGKS : (p->scheme == DVBE_BKG ? SC_BKG_FV : SC_CFREE);
   if (p->bkg_fd) {
     if (p->scheme != DVBE_BKG || !pb.per_x || !pb.per_y || !uniform(pb.xf) || !uniform(pb.yf))
       return fail(DVBE_ERR_UNSUPPORTED,
@@ -218,6 +218,14 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   faces(pb.yf, ycb, pb.yfth, pb.yfs);
   cols(pb.xf, xcb, pb.xct, pb.xcu);
   cols(pb.yf, ycb, pb.yct, pb.ycu);
+  if (p->scheme == DVBE_CFREE_CENTRAL) {
+    // Eq. cfd1: the face value at x_b itself, no shift along the
+    // characteristic: normal and tangential slope factors vanish
+    std::fill(pb.xfs.begin(), pb.xfs.end(), 0.0);
+    std::fill(pb.yfs.begin(), pb.yfs.end(), 0.0);
+    std::fill(pb.xct.begin(), pb.xct.end(), 0.0);
+    std::fill(pb.yct.begin(), pb.yct.end(), 0.0);
+  }
   pb.ext[0] = (xcb[0] - xcb[1]) / (xcb[1] - xcb[2]);
   pb.ext[1] = (xcb[nx + 1] - xcb[nx]) / (xcb[nx] - xcb[nx - 1]);
   pb.ext[2] = (ycb[0] - ycb[1]) / (ycb[1] - ycb[2]);
@@ -251,6 +259,10 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   if (pb.user_scheme == DVBE_DUGKS) {
     pb.a_phi = (2 * tau - h) / (2 * tau + dt);
     pb.b_phi = 3 * h / (2 * tau + dt);
+  } else if (pb.kernel == SC_CFREE) {
+    // the cell f^n = (2 tau f_tilde + dt f_eq) / (2 tau + dt)
+    pb.a_phi = 2 * tau / (2 * tau + dt);
+    pb.b_phi = dt / (2 * tau + dt);
   } else {
     pb.a_phi = (2 * tau - dt) / (2 * tau + dt);
     pb.b_phi = 2 * dt / (2 * tau + dt);

@@ -14,8 +14,10 @@ enum StoreMode { ST_F64 = 0, ST_F32 = 1, ST_F32_DEV = 2, ST_F16_DEV = 3, ST_BF16
 
 // Kernel variants: the DUGKS flux (Sec 2.2), the BKG flux in finite-volume
 // form (Eq. bkg_fv with the face values of Eq. f_left generalised to
-// stretched meshes), and BKG as the Lax-Wendroff stencil (Eq. bkgfd).
-enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2 };
+// stretched meshes), BKG as the Lax-Wendroff stencil (Eq. bkgfd), and the
+// collision-free faces of Sec 2.4 (Eqs. cfd1, cfd2: the cell f^n reconstructed
+// and used as the flux distribution; central = zero slopes in the tables).
+enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2, SC_CFREE = 3 };
 
 // Strip geometry.  A warp's lanes hold lane_cols adjacent columns each (two
 // for FP32 arithmetic, which then issues paired FP32 instructions; one for

@@ -416,6 +416,8 @@ __device__ __forceinline__ void dugks_face(V (&fb)[9], V rho0, V q) {
   }
 }
 
+// Face values each scheme needs: DUGKS all nine (for the face moments), the
+// others only the directions crossing the face.
 template <int SCHEME> __host__ __device__ constexpr bool needx(int a) {
   return SCHEME == SC_DUGKS ? true : EX(a) != 0;
 }
@@ -607,6 +609,7 @@ template <int SCHEME, int ST> struct Strip {
   using P = Pipe<ES, NC>;
   static constexpr bool DUG = SCHEME == SC_DUGKS;
   static constexpr bool FD = SCHEME == SC_BKG_FD;
+  static constexpr bool CF = SCHEME == SC_CFREE;
 
   const CaseArgs &A;
   K<V> k;
@@ -1087,6 +1090,13 @@ template <int SCHEME, int ST> struct Strip {
         read_row<INT>(stj, d);
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = vfma(Pb[a] - d[a], V(Real(1.0 / 3.0)), Pb[a]);
+      } else if constexpr (CF) {
+        // collision-free faces: phi = f^n = (f_tilde + f_tilde^+) / 2, so
+        // f_tilde^+ = phi + (phi - d)
+        V d[9];
+        read_row<INT>(stj, d);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = Pb[a] + (Pb[a] - d[a]);
       } else {
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = Pb[a];
@@ -1307,8 +1317,10 @@ cudaError_t launch_step_impl(int scheme, const CaseArgs &a, int blocks, int wpb,
   const int smem = wpb * warp_smem<ST>();
   const long long nitems = (long long)a.strips_x * a.strips_y;
   if (blocks <= 0) blocks = (int)((nitems + wpb - 1) / wpb);
-  auto kern = scheme == SC_DUGKS ? dev::k_step<SC_DUGKS, ST>
-                                 : (scheme == SC_BKG_FV ? dev::k_step<SC_BKG_FV, ST> : dev::k_step<SC_BKG_FD, ST>);
+  auto kern = scheme == SC_DUGKS    ? dev::k_step<SC_DUGKS, ST>
+              : scheme == SC_BKG_FV ? dev::k_step<SC_BKG_FV, ST>
+              : scheme == SC_BKG_FD ? dev::k_step<SC_BKG_FD, ST>
+                                    : dev::k_step<SC_CFREE, ST>;
   cudaError_t e = allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, block, smem, s>>>(a);

@@ -245,6 +245,71 @@ def test_torch_allocator_and_stream(dv):
 
 # ------------------------------------------------------------------ precision modes
 
+# ------------------------------------------- collision-free faces (Sec 2.4)
+
+CFREE = ["cfree_upwind", "cfree_central"]
+
+
+@pytest.mark.parametrize("scheme", CFREE)
+def test_collision_free_faces_periodic(dv, scheme):
+    """Eqs. cfd2 / cfd1: random state on a ragged periodic 67 x 23 mesh and on a
+    random stretched mesh, against the oracle."""
+    g, o = run_pair(dv, periodic_case(67, 23, scheme), 50, seed=11, launch=dict(strip_rows=7))
+    assert rel_err(g, o) < TOL64
+    rng = np.random.default_rng(12)
+    xf = np.concatenate([[0], np.cumsum(rng.uniform(0.5, 1.5, 45))]) / 45
+    yf = np.concatenate([[0], np.cumsum(rng.uniform(0.5, 1.5, 38))]) / 38
+    g, o = run_pair(dv, periodic_case(45, 38, scheme, xf=xf, yf=yf, tau=0.005), 50, seed=13)
+    assert rel_err(g, o) < TOL64
+
+
+@pytest.mark.parametrize("scheme", CFREE)
+@pytest.mark.parametrize("kind", ["wall", "diffuse"])
+def test_collision_free_faces_walls(dv, scheme, kind):
+    """Walls, the moving lid and the free-stream boundaries with collision-free
+    faces: stretched cavity and flat plate against the oracle."""
+    case, fields = W.cavity(40, Re=400, scheme=scheme, stretch_beta=1.5, kind=kind)
+    g, o = run_pair(dv, case, 50, fields=fields, launch=dict(strip_rows=16))
+    assert rel_err(g, o) < TOL64
+    case, fields = W.flat_plate(nx_up=12, nx_plate=40, ny=26, scheme=scheme)
+    g, o = run_pair(dv, case, 50, fields=fields, launch=dict(strip_rows=8))
+    assert rel_err(g, o) < TOL64
+
+
+@pytest.mark.parametrize("scheme", CFREE)
+def test_collision_free_faces_fp32(dv, scheme):
+    """FP32 arithmetic with FP32-deviation storage, same bound as the other
+    schemes (storage rounding of 2^-24 |delta| per step, 50 steps)."""
+    case, fields = W.taylor_green_box(64, u0=0.05, scheme=scheme)
+    g, o = run_pair(dv, case, 50, fields=fields, precision="f32_dev")
+    assert np.max(np.abs(g - o)) / np.max(np.abs(o)) < 1e-6
+
+
+def test_batch_rejects_collision_free_faces(dv):
+    case, _ = W.taylor_green_box(32, scheme="cfree_upwind")
+    with pytest.raises(dv.DvbeError) as e:
+        dv.Batch([case], precision="f32")
+    assert e.value.status == dv.DVBE_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ paired layout
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("nx", [2, 59, 60, 61, 120, 121])
+def test_strip_edges_paired_fp32(dv, scheme, nx):
+    """FP32 arithmetic holds two columns per lane and 60 output columns per
+    strip: mesh widths at and around those edges, periodic in x and walls in
+    y, then walls on all sides; FP32-deviation storage against the oracle."""
+    ny = 9
+    xf, yf = W.uniform_faces(nx, 0, nx / 16.0), W.uniform_faces(ny, 0, ny / 16.0)
+    for bcx in (_per(), [W.wall()]):
+        case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=W.RT_LATTICE, tau=0.01,
+                    dt=W.cfl_dt(xf, yf, 0.5), scheme=scheme,
+                    bc=[bcx, bcx, [W.wall()], [W.wall(0.05, 0.0)]])
+        g, o = run_pair(dv, case, 40, seed=2, precision="f32_dev", launch=dict(strip_rows=4))
+        assert np.max(np.abs(g - o)) / np.max(np.abs(o)) < 1e-6
+
+
 @pytest.mark.parametrize("precision,bound", [("f32", 1e-5), ("f32_dev", 1e-6),
                                              ("f16_dev", 3e-3), ("bf16_dev", 3e-2)])
 @pytest.mark.parametrize("scheme", ["dugks", "bkg"])
