@@ -40,7 +40,7 @@ def _stale(target: str, deps) -> bool:
 
 
 KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL",
-         "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL")
+         "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL", "DVBE_STAGES")
 
 
 def _flags():

@@ -57,6 +57,11 @@
 #ifndef DVBE_PAIR_BKG_UNROLL
 #define DVBE_PAIR_BKG_UNROLL 0
 #endif
+// Shared-memory stages of each warp's row pipeline (rows j and j+1 are held,
+// the others are in flight).
+#ifndef DVBE_STAGES
+#define DVBE_STAGES 5
+#endif
 
 namespace dvbe {
 namespace dev {
@@ -581,7 +586,7 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 template <int ES, int NC> struct Pipe {
   static constexpr int W = stage_cols(ES, NC); // columns per staged row
   static constexpr int WW = 16 / ES;           // columns of the periodic-wrap copies
-  static constexpr int NS = 5;                 // stages: rows j, j+1 held, three in flight
+  static constexpr int NS = DVBE_STAGES;       // stages: rows j, j+1 held, the rest in flight
   static constexpr int MAINB = ((9 * W * ES + 127) / 128) * 128;
   // periodic-wrap copies: a 9 x 16-byte box each (fields packed 16 bytes
   // apart); every tensor-copy destination sits on a 128-byte boundary
