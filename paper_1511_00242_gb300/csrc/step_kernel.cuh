@@ -240,15 +240,17 @@ template <> struct LaneT<float> {
 };
 
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-// Single precision: hardware approximation refined by one Newton-Raphson
-// step r <- r (2 - x r), within about one ulp of 1/x.
-__device__ __forceinline__ float rcp(float x) {
+// Single precision: the hardware approximation alone, within about one ulp
+// of 1/x.  1/rho only scales U = m / rho, which enters the cell stage through
+// the second-order term Q alone (mass and momentum come from rho' and m) and
+// the face equilibrium through the flux, which stays conservative; an ulp
+// there is below the rounding of the FP32 arithmetic around it.
+__device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  const float e = fmaf(-x, r, 1.0f);
-  return fmaf(r, e, r);
+  return r;
 }
-__device__ __forceinline__ F2 rcp(F2 x) { return F2(rcp(x.x), rcp(x.y)); }
+__device__ __forceinline__ F2 rcp(F2 x) { return F2(rcp_approx(x.x), rcp_approx(x.y)); }
 
 // Weight class of a direction: 0 rest, 1 axis, 2 diagonal.
 __host__ __device__ constexpr int WCLS(int a) { return a == 0 ? 0 : (a <= 4 ? 1 : 2); }
@@ -1077,11 +1079,12 @@ template <int SCHEME, int ST> struct Strip {
     const int q = j - rt.jb;
     const Real tyc = __shfl_sync(kFull, rt.tyc, q), cyu = __shfl_sync(kFull, rt.cyu, q);
     const Real th = __shfl_sync(kFull, rt.th, q), sl = __shfl_sync(kFull, rt.s, q);
+    bool last_staged = false;
     if (INT || !have_next) {
       if (INT || stored(j + 1)) {
         stn = wait();
         stage_row<INT>(INT ? j + 1 : wrapr(j + 1), stn, Pc);
-        if (j + 1 == jend) release<INT>(); // only phi of this row is needed
+        last_staged = j + 1 == jend; // only phi of this row is needed
       } else {
         ghost_row(3, Pb, Pa, Pc);
       }
@@ -1127,6 +1130,10 @@ template <int SCHEME, int ST> struct Strip {
       }
       store_row<INT>(j, v);
     }
+    // the stage of row j is free; on the strip's last row the stage of row
+    // j+1 too (released here rather than right after its cell stage, so that
+    // the cell stage, faces and update form one block for the scheduler)
+    if (last_staged) release<INT>();
     release<INT>();
     stj = stn;
   }
