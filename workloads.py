@@ -227,6 +227,19 @@ def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1
     return case, (np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx)))
 
 
+def flat_plate_paper(dy_min: float, cfl: float = 0.5, scheme: str = "dugks"):
+    """The flat-plate set-up of Sec 3.3: U0 = 0.1, L = 94.76, Re = 1e5; y cells
+    grow by 1.1 from dy_min, as many as needed for a height just above 50;
+    120 x cells, 80 on the plate, from dx_min = 0.1 at the leading edge,
+    growing by 1.1 upstream (40 cells) and, on the plate, by the ratio that
+    fits L (1.049, where the paper prints 1.05)."""
+    ny = int(math.ceil(math.log(1.0 + 50.0 * 0.1 / dy_min) / math.log(1.1)))
+    height = dy_min * (1.1 ** ny - 1.0) / 0.1
+    up_len = 0.1 * (1.1 ** 40 - 1.0) / 0.1
+    return flat_plate(nx_up=40, nx_plate=80, ny=ny, U=0.1, Re_L=1e5, L=94.76, dy_min=dy_min,
+                      height=height, up_len=up_len, dx_min=0.1, cfl=cfl, scheme=scheme)
+
+
 def solve_geometric_ratio(n: int, d0: float, length: float) -> float:
     """Ratio r with d0 (r^n - 1)/(r - 1) = length (bisection)."""
     if abs(d0 * n - length) <= 1e-15 * length:
