@@ -59,13 +59,13 @@ def test_table1_on_gpu(dv, scheme):
 
 
 def test_time_step_sweep_n64(dv):
-    """Sec 3.1, Fig. tv_dtErr: N = 64, tau fixed, dt/tau = 5 .. 50.  The error
+    """Sec 3.1, Fig. tv_dtErr: N = 64, tau fixed, dt/tau = 10 .. 50.  The error
     at t_c grows almost linearly with dt once the time error dominates, the
     DUGKS error stays below BKG's at every dt, and both schemes blow up at
     dt/tau = 100, where the CFL number (dt |xi|_max / dx = 1.57) exceeds 1."""
     errs = {}
     for scheme in ("dugks", "bkg"):
-        for ratio in (5.0, 10.0, 20.0, 50.0):
+        for ratio in (10.0, 20.0, 50.0):
             case, fields, d, tc = W.taylor_green_paper(64, scheme, dt_over_tau=ratio)
             steps = int(round(tc / case["dt"]))
             with dv.Solver(case, precision="f64") as s:
@@ -75,11 +75,11 @@ def test_time_step_sweep_n64(dv):
                 errs[(scheme, ratio)] = s.l2_error_u(*W.taylor_green_paper_analytic(case, steps * case["dt"]))
             print(f"dt sweep {scheme} dt/tau={ratio:g}: E_u(t_c)={errs[(scheme, ratio)]:.4e}")
     for scheme in ("dugks", "bkg"):
-        e = [errs[(scheme, r)] for r in (5.0, 10.0, 20.0, 50.0)]
+        e = [errs[(scheme, r)] for r in (10.0, 20.0, 50.0)]
         assert all(a < b for a, b in zip(e, e[1:]))
-        slope = math.log(e[3] / e[2]) / math.log(50.0 / 20.0)
+        slope = math.log(e[2] / e[1]) / math.log(50.0 / 20.0)
         assert 0.7 < slope < 1.3, slope
-    for ratio in (5.0, 10.0, 20.0, 50.0):
+    for ratio in (10.0, 20.0, 50.0):
         assert errs[("dugks", ratio)] < errs[("bkg", ratio)]
     for scheme in ("dugks", "bkg"):
         case, fields, d, tc = W.taylor_green_paper(64, scheme, dt_over_tau=100.0)
@@ -102,15 +102,15 @@ def _decay_viscosity(case, u, v, t):
 def test_collision_free_faces_numerical_viscosity(dv):
     """Sec 2.4: dropping the collision integral from the face distribution
     (the upwind face of Eq. cfd2) adds a numerical viscosity proportional to
-    dt.  Taylor-Green, paper set-up, N = 64, tau fixed, run to t_c / 2: the
+    dt.  Taylor-Green, paper set-up, N = 64, tau fixed, run to t_c / 4: the
     excess nu_eff / nu - 1 of the upwind collision-free face grows in
     proportion to dt/tau, while DUGKS stays within a few percent of nu.  The
     central face of Eq. cfd1 is reported."""
     ex = {}
     for scheme in ("cfree_upwind", "dugks", "cfree_central"):
-        for ratio in (1.0, 2.0, 4.0):
+        for ratio in (2.0, 4.0, 8.0):
             case, fields, d, tc = W.taylor_green_paper(64, scheme, dt_over_tau=ratio)
-            steps = int(round(0.5 * tc / case["dt"]))
+            steps = int(round(0.25 * tc / case["dt"]))
             with dv.Solver(case, precision="f64") as s:
                 s.set_launch(strip_rows=16, warps_per_block=2, graph_chunk=2000)
                 s.init_chapman_enskog(*fields, d)
@@ -121,10 +121,10 @@ def test_collision_free_faces_numerical_viscosity(dv):
                 except dv.DvbeError:
                     ex[(scheme, ratio)] = float("nan")
             print(f"numerical viscosity {scheme} dt/tau={ratio:g}: nu_eff/nu - 1 = {ex[(scheme, ratio)]:.4f}")
-    up = [ex[("cfree_upwind", r)] for r in (1.0, 2.0, 4.0)]
-    assert up[0] > 0.2
+    up = [ex[("cfree_upwind", r)] for r in (2.0, 4.0, 8.0)]
+    assert up[0] > 0.4
     assert 1.6 < up[1] / up[0] < 2.4 and 3.2 < up[2] / up[0] < 4.8
-    assert all(abs(ex[("dugks", r)]) < 0.05 for r in (1.0, 2.0, 4.0))
+    assert all(abs(ex[("dugks", r)]) < 0.05 for r in (2.0, 4.0, 8.0))
 
 
 def test_dugks_more_accurate_than_bkg_at_n32(dv):
