@@ -174,7 +174,9 @@ DVBE_API dvbe_status dvbe_init_chapman_enskog(dvbe_solver s, const double *rho, 
 DVBE_API dvbe_status dvbe_init_f(dvbe_solver s, const double *f_tilde);
 DVBE_API dvbe_status dvbe_get_f(dvbe_solver s, double *f_tilde);
 
-/* Advance nsteps time steps (Eq. eq_update for DUGKS, Eq. lwfv for BKG).
+/* Advance nsteps time steps (Eq. eq_update for DUGKS, Eq. lwfv for BKG, the
+ * same finite-volume update with the collision-free faces of Eqs. cfd1 /
+ * cfd2 for DVBE_CFREE_*).
  * Launches are queued on the solver's stream; the call then waits for them
  * and returns DVBE_ERR_DIVERGED if any step met a non-finite or non-positive
  * density (the state is left as it is). */
