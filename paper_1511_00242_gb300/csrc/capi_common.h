@@ -25,7 +25,7 @@ struct Problem {
   std::vector<double> xfth, xfs, xct, xcu, yfth, yfs, yct, ycu, volx, voly;
   double ext[4] = {0, 0, 0, 0};
   std::vector<unsigned char> segid[4];
-  double a_phi = 0, b_phi = 0, a_tp = 0, b_tp = 0, p_face = 0, q_face = 0, fd_nux = 0, fd_nuy = 0;
+  double b_phi = 0, q_face = 0, fd_nux = 0, fd_nuy = 0; // transform coefficients (increment forms)
   int pitch = 0, elem = 0;
   long long plane = 0;
 };

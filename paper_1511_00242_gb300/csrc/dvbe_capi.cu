@@ -256,21 +256,14 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   // f_tilde / f_tilde^+ transforms of Sec 2.2)
   const double tau = pb.tau, dt = pb.dt;
   pb.c = c;
-  if (pb.user_scheme == DVBE_DUGKS) {
-    pb.a_phi = (2 * tau - h) / (2 * tau + dt);
-    pb.b_phi = 3 * h / (2 * tau + dt);
-  } else if (pb.kernel == SC_CFREE) {
-    // the cell f^n = (2 tau f_tilde + dt f_eq) / (2 tau + dt)
-    pb.a_phi = 2 * tau / (2 * tau + dt);
-    pb.b_phi = dt / (2 * tau + dt);
-  } else {
-    pb.a_phi = (2 * tau - dt) / (2 * tau + dt);
-    pb.b_phi = 2 * dt / (2 * tau + dt);
-  }
-  pb.a_tp = (2 * tau - dt) / (2 * tau + dt);
-  pb.b_tp = 2 * dt / (2 * tau + dt);
-  pb.p_face = 2 * tau / (2 * tau + h);
-  pb.q_face = h / (2 * tau + h);
+  // increment forms phi = f_tilde + b (f_eq - f_tilde), f = f_bar + q (f_eq - f_bar)
+  if (pb.user_scheme == DVBE_DUGKS)
+    pb.b_phi = 3 * h / (2 * tau + dt); // f_bar^+ = ((2 tau - h) f_tilde + 3 h f_eq) / (2 tau + dt)
+  else if (pb.kernel == SC_CFREE)
+    pb.b_phi = dt / (2 * tau + dt); // the cell f^n = (2 tau f_tilde + dt f_eq) / (2 tau + dt)
+  else
+    pb.b_phi = 2 * dt / (2 * tau + dt); // f_tilde^+ = ((2 tau - dt) f_tilde + 2 dt f_eq) / (2 tau + dt)
+  pb.q_face = h / (2 * tau + h);        // f = (2 tau f_bar + h f_eq) / (2 tau + h)
   pb.fd_nux = c * dt / (pb.xf[1] - pb.xf[0]);
   pb.fd_nuy = c * dt / (pb.yf[1] - pb.yf[0]);
   // storage layout: rows padded to 128 bytes and at least 64 elements, so a
@@ -342,11 +335,7 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   a.per_x = pb.per_x;
   a.per_y = pb.per_y;
   a.rho0 = pb.rho0;
-  a.a_phi = pb.a_phi;
   a.b_phi = pb.b_phi;
-  a.a_tp = pb.a_tp;
-  a.b_tp = pb.b_tp;
-  a.p_face = pb.p_face;
   a.q_face = pb.q_face;
   for (int c = 0; c < 3; ++c) a.dev_scale[c] = pb.scale[c];
   a.fd_nux = pb.fd_nux;

@@ -60,9 +60,9 @@ struct CaseArgs {
   int strips_x, strips_y, H; // strip decomposition: strip_cols columns x H rows per warp
 
   double rho0;
-  double a_phi, b_phi;   // phi = a delta + b delta_eq   (DUGKS: f_bar^+, BKG: f_tilde^+)
-  double a_tp, b_tp;     // f_tilde^+ = a delta + b delta_eq (DUGKS update)
-  double p_face, q_face; // DUGKS face: f = p f_bar + q f_eq
+  double b_phi;          // phi = delta + b (delta_eq - delta): DUGKS f_bar^+, BKG f_tilde^+,
+                         // collision-free faces f^n
+  double q_face;         // DUGKS face: f = f_bar + q (f_eq - f_bar)
   double dev_scale[3];   // deviation storage scale per weight class (rest, axis, diagonal)
   double fd_nux, fd_nuy; // BKG-FD: c dt / dx, c dt / dy (uniform meshes)
 

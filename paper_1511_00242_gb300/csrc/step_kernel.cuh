@@ -161,18 +161,6 @@ __device__ __forceinline__ double to_real(double x) { return x; }
 __device__ __forceinline__ float to_real(float x) { return x; }
 __device__ __forceinline__ float to_real(__half x) { return __half2float(x); }
 __device__ __forceinline__ float to_real(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <typename T> __device__ __forceinline__ T from_real(double x);
-template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
-template <typename T> __device__ __forceinline__ T from_realf(float x);
-template <> __device__ __forceinline__ float from_realf<float>(float x) { return x; }
-template <> __device__ __forceinline__ __half from_realf<__half>(float x) { return __float2half_rn(x); }
-template <> __device__ __forceinline__ __nv_bfloat16 from_realf<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
-}
-__device__ __forceinline__ void store_real(double *p, double v) { *p = v; }
-template <typename T> __device__ __forceinline__ void store_real(T *p, float v) {
-  *p = from_realf<T>(v);
-}
 
 // ---- lane vectors -------------------------------------------------------------
 // A lane holds the values of NC adjacent columns: V = double (NC = 1) for FP64
@@ -442,13 +430,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
 }
 // 3-d tiled bulk tensor copy global -> shared, completion on an mbarrier.
 __device__ __forceinline__ void tma_load3(uint32_t dst, const void *tmap, int x, int y, int z,
