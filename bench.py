@@ -239,6 +239,22 @@ def accuracy(dv, scheme, precision, n=256):
             "E_vs_fp64": ep, "E_fp64_vs_analytic": ed, "ratio": ep / ed, "bar": 0.1}
 
 
+def stability_map(meshes=(32, 64), cfls=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.05), iters=10, t_end=100.0):
+    """Largest stable dt/tau of the lid-driven cavity (impulsive start, lid
+    U = 0.1 c) against the CFL number, both schemes, one JSON line per point:
+    the bisection bracket [lo, hi] after `iters` iterations over [0.5, 1e4],
+    each trial run to t = t_end (L / U = 10)."""
+    from paper_1511_00242_gb300.stability import bisect_max_ratio
+    points = [(s, n, c) for s in ("dugks", "bkg") for n in meshes for c in cfls]
+    t0 = time.perf_counter()
+    res = bisect_max_ratio(W.cavity_at_ratio, points, lo=0.5, hi=1e4, iters=iters, t_end=t_end)
+    for r in res:
+        r.pop("trials")
+        scheme, n, cfl = r.pop("point")
+        print(json.dumps(dict(scheme=scheme, mesh=n, cfl=cfl, **r)), flush=True)
+    print(json.dumps({"stability_map_seconds": time.perf_counter() - t0}), flush=True)
+
+
 def cpu_baseline(scheme, budget_s=12.0):
     """The FP64 oracle as it stands, one host thread, on a 512 x 512 sample of
     the same Taylor-Green workload, stepped until ~budget_s seconds are spent."""

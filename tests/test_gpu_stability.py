@@ -22,7 +22,7 @@ def dv():
 def test_cavity_stability_map_32(dv):
     from paper_1511_00242_gb300.stability import bisect_max_ratio
     points = [("dugks", 32, 0.5), ("dugks", 32, 0.9), ("bkg", 32, 0.5), ("bkg", 32, 0.9)]
-    res = bisect_max_ratio(W.cavity_at_ratio, points, lo=0.5, hi=1e4, rounds=8, t_end=50.0)
+    res = bisect_max_ratio(W.cavity_at_ratio, points, lo=0.5, hi=1e4, iters=8, t_end=50.0)
     by = {}
     for r in res:
         print(f"stability {r['point']}: max stable dt/tau in [{r['lo']:.4g}, {r['hi']}]"
