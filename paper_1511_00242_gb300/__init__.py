@@ -226,7 +226,8 @@ def make_params(case: dict, mesh, precision="f64", stream=None, allow_cfl_ge_1=F
     p.mesh = mesh
     p.RT, p.tau, p.dt = float(case["RT"]), float(case["tau"]), float(case["dt"])
     p.rho0 = float(rho0)
-    p.scheme = SCHEMES[case.get("scheme", "dugks")]
+    sc = case.get("scheme", "dugks")
+    p.scheme = SCHEMES[sc] if isinstance(sc, str) else int(sc)
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     keep = []
     for side in range(4):

@@ -82,4 +82,9 @@ def test_validation_before_device_work(dv):
     assert _create_status(dv, gap) == dv.DVBE_ERR_INVALID_ARG  # S side not covered
     cav, _ = W.cavity(16)
     assert _create_status(dv, dict(cav, scheme="bkg"), bkg_fd=True) == dv.DVBE_ERR_UNSUPPORTED
+    # the finite-difference form is BKG only, not the collision-free faces
+    assert _create_status(dv, dict(case, scheme="cfree_upwind"), bkg_fd=True) == dv.DVBE_ERR_UNSUPPORTED
+    # scheme codes beyond the four of dvbe_scheme
+    assert _create_status(dv, dict(case, scheme=4)) == dv.DVBE_ERR_INVALID_ARG
+    assert _create_status(dv, dict(case, scheme=-1)) == dv.DVBE_ERR_INVALID_ARG
     assert "CFL" in (lambda: (_create_status(dv, bad), dv.dvbe_last_error())[1])()
