@@ -1,6 +1,6 @@
 // Batched form of libdvbe: many independent cases of uneven size advanced
 // together.  Each step is one persistent launch per scheme; its warps pull
-// strips (30 columns x H rows of one case) from a device work queue that
+// strips (strip_cols columns x H rows of one case) from a device work queue that
 // covers every case, so small and large meshes share the GPU without a
 // launch per case.  Steps are replayed from captured CUDA graphs.  A case
 // whose density turns non-finite is flagged and skipped from then on; the

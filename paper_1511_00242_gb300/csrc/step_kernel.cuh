@@ -1,18 +1,24 @@
 // Fused D2Q9 finite-volume step (DUGKS, Sec 2.2; BKG, Sec 2.3) for sm_103a.
 //
-// Work decomposition.  A warp owns a strip of 32 consecutive columns
-// (output columns i0 .. i0+29 plus one halo column on each side) and marches
-// up through H rows.  Each lane keeps the reconstruction variable phi of its
-// own column for rows j-1, j, j+1 in registers; values of the neighbouring
-// columns come from warp shuffles.  Nothing goes through shared memory and no
-// block-wide barrier is needed.  Per row and lane:
+// Work decomposition.  A warp owns a strip of consecutive columns and marches
+// up through H rows.  With FP32 arithmetic each lane holds two adjacent
+// columns as a float pair, whose arithmetic issues as paired (.f32x2)
+// instructions: 64 columns, outputs i0 .. i0+59, two halo columns on each
+// side of which the inner one is used.  With FP64 each lane holds one
+// column: 32 columns, outputs i0 .. i0+29.  Each lane keeps the
+// reconstruction variable phi of its columns for rows j-1, j, j+1 in
+// registers; values of the neighbouring columns come from warp shuffles.
+// Rows arrive through a per-warp ring of tensor copies into shared memory;
+// lanes exchange nothing through it, and no block-wide barrier is needed.
+// Per row and column:
 //   1. load f_tilde of row j+1 (9 coalesced loads), cell stage:
 //      rho, u (Eq. macro_var), f_eq (Eq. equilibrium),
 //      phi = f_bar^+ (DUGKS, Eq. eq_trans_2) or f_tilde^+ (BKG, Eq. bkg_collision)
 //   2. ghost values of phi at non-periodic sides (Sec 2.5)
-//   3. the x-face west of the lane's cell: phi(x_b - h xi) by linear
+//   3. the x-face west of the cell: phi(x_b - h xi) by linear
 //      reconstruction (Eqs. eq_char / bkg_fb; on a uniform mesh Eq. f_left),
-//      split into a left part computed by the left lane and a right part,
+//      split into a left part computed for the column to the left and a
+//      right part,
 //   4. the y-face north of the cell (the south face is the previous row's
 //      north face, kept in registers),
 //   5. boundary faces: bounce-back / diffuse wall / inflow (Sec 2.5),

@@ -2,7 +2,8 @@
 
 FP64 bar: relative max error on f_tilde <= 1e-12 after 100 steps (the
 arithmetic differs from the oracle only in the order of rounding).  Sizes
-span several 30-column strips and several row strips with ragged tails.
+span several strips (30 columns in FP64, 60 in FP32) and several row strips
+with ragged tails.
 Lower precisions are held to bounds derived from their storage rounding
 (see test_precision_modes_error_bounds)."""
 import math
