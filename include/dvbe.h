@@ -82,7 +82,11 @@ typedef enum {
   DVBE_BC_INFLOW_EQ = 3,       /* free stream: ghosts f_eq(rho, ux, uy); at the
                                   face the entering distributions take it      */
   DVBE_BC_OUTFLOW_ZG = 4,      /* zero-gradient ghosts                          */
-  DVBE_BC_SYMMETRY = 5         /* mirrored ghosts                               */
+  DVBE_BC_SYMMETRY = 5,        /* mirrored ghosts                               */
+  DVBE_BC_OUTFLOW_NEQ = 6      /* outflow at the segment's density rho: ghost =
+                                  inner value + f_eq(rho, u_1) - f_eq(rho_1, u_1)
+                                  (not in the paper; bounded at small dt/tau
+                                  where the zero-gradient outflow may not be) */
 } dvbe_bc_kind;
 
 /* A segment of one side: faces whose centre coordinate along the side lies in

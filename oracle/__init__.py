@@ -25,7 +25,8 @@ _SRC = os.path.join(_HERE, "dvbe_oracle.c")
 _HDR = os.path.join(_HERE, "dvbe_oracle.h")
 _SO = os.path.join(_HERE, "liboracle.so")
 
-KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5}
+KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5,
+         "outflow_neq": 6}
 SCHEMES = {"dugks": 0, "bkg": 1, "cfree_upwind": 2, "cfree_central": 3}
 
 

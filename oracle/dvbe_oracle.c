@@ -40,6 +40,12 @@
  *     at the boundary face, the distributions entering the domain are set
  *     to it (those leaving keep their reconstructed values); outflow:
  *     zero-gradient ghosts; symmetry: mirrored ghosts.
+ *   - Outflow at a set density (not in the paper; an option beside the
+ *     zero-gradient outflow): the ghost is the first inner value with its
+ *     equilibrium part taken at the segment's density, f_eq(rho_s, u_1)
+ *     + (phi_1 - f_eq(rho_1, u_1)).  It holds the outlet at that density;
+ *     on the flat plate at small dt/tau it stays bounded where the
+ *     zero-gradient outflow diverges.
  */
 #include "dvbe_oracle.h"
 
@@ -224,7 +230,7 @@ static const orc_bc_segment *seg_at(const orc_problem *p, int side, double t) {
   return NULL;
 }
 
-static int kind_valid(int k) { return k >= ORC_BC_PERIODIC && k <= ORC_BC_SYMMETRY; }
+static int kind_valid(int k) { return k >= ORC_BC_PERIODIC && k <= ORC_BC_OUTFLOW_NEQ; }
 
 static int geom_build(const orc_problem *p, geom *g) {
   memset(g, 0, sizeof(*g));
@@ -330,6 +336,17 @@ static void ghost_rule(const vset *v, const orc_bc_segment *s, double e, const i
     case ORC_BC_OUTFLOW_ZG:
       for (int a = 0; a < 9; ++a) pg[a] = p1[a];
       break;
+    case ORC_BC_OUTFLOW_NEQ: {
+      /* the first inner value with its equilibrium part moved from rho_1 to
+         the segment's density at the same velocity:
+         pg = p1 + f_eq(rho_s, u_1) - f_eq(rho_1, u_1) */
+      double r1, ux1, uy1, e1[9], es[9];
+      moments_of(v, p1, &r1, &ux1, &uy1);
+      feq_of(v, r1, ux1, uy1, e1);
+      feq_of(v, s->rho, ux1, uy1, es);
+      for (int a = 0; a < 9; ++a) pg[a] = p1[a] + (es[a] - e1[a]);
+      break;
+    }
     case ORC_BC_SYMMETRY:
       for (int a = 0; a < 9; ++a) pg[a] = p1[mir[a]];
       break;

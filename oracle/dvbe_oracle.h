@@ -45,7 +45,9 @@ enum {
   ORC_BC_WALL_DIFFUSE = 2,
   ORC_BC_INFLOW_EQ = 3,
   ORC_BC_OUTFLOW_ZG = 4,
-  ORC_BC_SYMMETRY = 5
+  ORC_BC_SYMMETRY = 5,
+  ORC_BC_OUTFLOW_NEQ = 6 /* outflow at the segment's density: equilibrium part at rho_s,
+                            non-equilibrium part extrapolated (zero gradient) */
 };
 
 enum { ORC_SIDE_W = 0, ORC_SIDE_E = 1, ORC_SIDE_S = 2, ORC_SIDE_N = 3 };

@@ -27,7 +27,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdvbe.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "dvbe.h")
 
-KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5}
+KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5,
+         "outflow_neq": 6}
 SCHEMES = {"dugks": 0, "bkg": 1, "cfree_upwind": 2, "cfree_central": 3}
 PRECISIONS = {"f64": 0, "f32": 1, "f32_dev": 2, "f16_dev": 3, "bf16_dev": 4}
 STATUS = {0: "DVBE_OK", 1: "DVBE_ERR_INVALID_ARG", 2: "DVBE_ERR_CFL", 3: "DVBE_ERR_OOM",

@@ -141,11 +141,11 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
     pb.bc[s].assign(p->bc[s], p->bc[s] + p->nbc[s]);
     per[s] = false;
     for (auto &g : pb.bc[s]) {
-      if (g.kind < DVBE_BC_PERIODIC || g.kind > DVBE_BC_SYMMETRY)
+      if (g.kind < DVBE_BC_PERIODIC || g.kind > DVBE_BC_OUTFLOW_NEQ)
         return fail(DVBE_ERR_INVALID_ARG, "unknown boundary kind");
       if (g.kind == DVBE_BC_PERIODIC) per[s] = true;
-      if (g.kind == DVBE_BC_INFLOW_EQ && !(g.rho > 0))
-        return fail(DVBE_ERR_INVALID_ARG, "inflow density must be positive");
+      if ((g.kind == DVBE_BC_INFLOW_EQ || g.kind == DVBE_BC_OUTFLOW_NEQ) && !(g.rho > 0))
+        return fail(DVBE_ERR_INVALID_ARG, "inflow / outflow density must be positive");
     }
     if (per[s] && p->nbc[s] != 1)
       return fail(DVBE_ERR_INVALID_ARG, "a periodic side takes exactly one segment");

@@ -343,6 +343,25 @@ __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho
   } else if (kind == DVBE_BC_OUTFLOW_ZG) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = p1[a];
+  } else if (kind == DVBE_BC_OUTFLOW_NEQ) {
+    // the first inner value with its equilibrium part at the segment's
+    // density: g = p1 + f_eq(rho_s, U_1) - f_eq(rho_1, U_1)
+    //            = p1 + w (rho_s - rho_1) (1 + P(U_1))
+    Real rp = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      rp += p1[a];
+      mx += Real(EX(a)) * p1[a];
+      my += Real(EY(a)) * p1[a];
+    }
+    const Real rho1 = rho0 + rp, Ux = mx / rho1, Uy = my / rho1;
+    const Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy), dr = Real(sp.rho) - rho1;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const Real eU = Real(EX(a)) * Ux + Real(EY(a)) * Uy;
+      const Real P = eU * (Real(3) + Real(4.5) * eU) - u15;
+      g[a] = p1[a] + Real(WGT(a)) * dr * (Real(1) + P);
+    }
   } else if (kind == DVBE_BC_SYMMETRY) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = p1[XSIDE ? MIRX(a) : MIRY(a)];

@@ -246,6 +246,25 @@ def test_torch_allocator_and_stream(dv):
 
 # ------------------------------------------------------------------ precision modes
 
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_set_density_outflow(dv, scheme):
+    """Outflow at a set density (east side of the flat plate; both sides of a
+    channel with fluid at another density) against the oracle, FP64 and
+    FP32-deviation storage."""
+    case, fields = W.flat_plate(nx_up=12, nx_plate=40, ny=26, scheme=scheme, outflow="outflow_neq")
+    g, o = run_pair(dv, case, 60, fields=fields, launch=dict(strip_rows=8))
+    assert rel_err(g, o) < TOL64
+    xf, yf = W.uniform_faces(70, 0.0, 1.0), W.uniform_faces(9, 0.0, 9 / 70)
+    side = [("outflow_neq", -W.INF, W.INF, 1.0, 0.0, 0.0)]
+    chan = dict(nx=70, ny=9, xf=xf, yf=yf, RT=W.RT_LATTICE, tau=0.01, dt=W.cfl_dt(xf, yf, 0.5),
+                scheme=scheme, bc=[side, side, _per(), _per()])
+    fields = (np.full((9, 70), 1.02), np.full((9, 70), 0.02), np.zeros((9, 70)))
+    for precision, bound in (("f64", TOL64), ("f32_dev", 1e-6)):
+        g, o = run_pair(dv, chan, 40, fields=fields, precision=precision, launch=dict(strip_rows=4))
+        err = rel_err(g, o) if precision == "f64" else float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+        assert err < bound, (precision, err)
+
+
 # ------------------------------------------- collision-free faces (Sec 2.4)
 
 CFREE = ["cfree_upwind", "cfree_central"]

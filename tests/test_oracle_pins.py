@@ -349,6 +349,36 @@ def test_free_stream_boundaries_keep_uniform_flow(scheme):
     case["bc"][2] = [("symmetry", -W.INF, W.INF, 1.0, 0.0, 0.0)]
     f0 = O.init_equilibrium(case, r, u, v)
     assert np.max(np.abs(O.step(case, f0, 50) - f0)) < 1e-16
+    # the set-density outflow at the free-stream density keeps it too
+    case["bc"][1] = [("outflow_neq", -W.INF, W.INF, 1.0, 0.0, 0.0)]
+    assert np.max(np.abs(O.step(case, f0, 50) - f0)) < 1e-16
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_set_density_outflow_acts_locally(scheme):
+    """Fluid at rest at rho = 1.01 between set-density outflows at rho_s = 1
+    (W, E; periodic in y).  The zero-gradient outflow keeps this state
+    exactly; the set-density one lowers the density of the cells next to the
+    outflows only, after one step (the stencil reaches one cell), and the
+    ghost value at rest is f_eq(rho_s, 0) plus the inner non-equilibrium part,
+    which is zero here."""
+    n = 10
+    xf, yf = W.uniform_faces(n, 0.0, 1.0), W.uniform_faces(4, 0.0, 0.4)
+    per = [("periodic", -W.INF, W.INF, 0.0, 0.0, 0.0)]
+
+    def case(kind):
+        side = [(kind, -W.INF, W.INF, 1.0, 0.0, 0.0)]
+        return dict(nx=n, ny=4, xf=xf, yf=yf, RT=RT, tau=0.01, dt=W.cfl_dt(xf, yf, 0.5),
+                    scheme=scheme, bc=[side, side, per, per])
+
+    r = np.full((4, n), 1.01)
+    z = np.zeros((4, n))
+    f0 = O.init_equilibrium(case("outflow"), r, z, z)
+    assert np.max(np.abs(O.step(case("outflow"), f0, 1) - f0)) < 1e-16
+    c = case("outflow_neq")
+    rho1, _, _ = O.moments(c, O.step(c, f0, 1))
+    assert np.all(rho1[:, 0] < 1.01) and np.all(rho1[:, -1] < 1.01)
+    assert np.max(np.abs(rho1[:, 1:-1] - 1.01)) < 1e-15
 
 
 # ---------------------------------------------------------------- physics
@@ -437,6 +467,9 @@ MUTATIONS = {
     # the collision-free faces reconstructing f_tilde^+ instead of f^n
     "cfree_phi": ("phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);",
                   "phi = tplus;"),
+    # the set-density outflow moving the ghost's density the wrong way
+    "outflow_neq_sign": ("for (int a = 0; a < 9; ++a) pg[a] = p1[a] + (es[a] - e1[a]);",
+                         "for (int a = 0; a < 9; ++a) pg[a] = p1[a] - (es[a] - e1[a]);"),
     # transposed theta in the y-face blend
     "theta_swap": ("double value = (1.0 - th) * pl + th * pr;\n    double slope_n = (pr - pl) / (yr - yl);",
                    "double value = th * pl + (1.0 - th) * pr;\n    double slope_n = (pr - pl) / (yr - yl);"),
@@ -479,6 +512,7 @@ def _pins_with(so_path):
             "linear_exact": lambda: test_linear_fields_advect_exactly_on_random_mesh("dugks"),
             "quadratic_central": lambda: test_quadratic_cell_averages_collisionless("cfree_central"),
             "cfree_identity": lambda: test_upwind_collision_free_face_identity(),
+            "outflow_neq": lambda: test_set_density_outflow_acts_locally("dugks"),
         }
         for k, fn in checks.items():
             try:

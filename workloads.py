@@ -190,15 +190,16 @@ def couette(nx: int, ny: int, U: float = 0.05, nu: float = 0.1, cfl: float = 0.5
 def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1,
                Re_L: float = 1e5, L: float = 1.0, dy_min: float | None = None,
                height: float = 0.5, up_len: float = 0.5, dx_min: float | None = None,
-               cfl: float = 0.5, scheme: str = "dugks"):
+               cfl: float = 0.5, scheme: str = "dugks", outflow: str = "outflow"):
     """Laminar boundary layer over a flat plate on 0 <= x <= L (Sec 3.3).
 
     Domain [-up_len, L] x [0, height].  y faces grow geometrically from dy_min
     with the ratio solved so that ny cells span exactly `height`; x faces are
     clustered at the leading edge by two geometric runs (upstream and along the
     plate), each ratio solved to fit its length.  Boundaries: inflow
-    equilibrium (west, north), zero-gradient outflow (east), symmetry before
-    the plate and a no-slip wall on it (south).  Fluid starts at the free stream.
+    equilibrium (west, north), zero-gradient outflow (east; `outflow` =
+    "outflow_neq" for the set-density outflow), symmetry before the plate and a
+    no-slip wall on it (south).  Fluid starts at the free stream.
     """
     nu = U * L / Re_L
     if dy_min is None:
@@ -219,7 +220,7 @@ def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1
     tau = nu / RT_LATTICE
     dt = cfl_dt(xf, yf, cfl)
     inflow = ("inflow", -INF, INF, 1.0, U, 0.0)
-    bc = [[inflow], [("outflow", -INF, INF, 1.0, 0.0, 0.0)],
+    bc = [[inflow], [(outflow, -INF, INF, 1.0, 0.0, 0.0)],
           [("symmetry", -INF, 0.0, 1.0, 0.0, 0.0), ("wall", 0.0, INF, 1.0, 0.0, 0.0)],
           [inflow]]
     case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=bc,
@@ -227,7 +228,7 @@ def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1
     return case, (np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx)))
 
 
-def flat_plate_paper(dy_min: float, cfl: float = 0.5, scheme: str = "dugks"):
+def flat_plate_paper(dy_min: float, cfl: float = 0.5, scheme: str = "dugks", outflow: str = "outflow"):
     """The flat-plate set-up of Sec 3.3: U0 = 0.1, L = 94.76, Re = 1e5; y cells
     grow by 1.1 from dy_min, as many as needed for a height just above 50;
     120 x cells, 80 on the plate, from dx_min = 0.1 at the leading edge,
@@ -237,7 +238,8 @@ def flat_plate_paper(dy_min: float, cfl: float = 0.5, scheme: str = "dugks"):
     height = dy_min * (1.1 ** ny - 1.0) / 0.1
     up_len = 0.1 * (1.1 ** 40 - 1.0) / 0.1
     return flat_plate(nx_up=40, nx_plate=80, ny=ny, U=0.1, Re_L=1e5, L=94.76, dy_min=dy_min,
-                      height=height, up_len=up_len, dx_min=0.1, cfl=cfl, scheme=scheme)
+                      height=height, up_len=up_len, dx_min=0.1, cfl=cfl, scheme=scheme,
+                      outflow=outflow)
 
 
 def solve_geometric_ratio(n: int, d0: float, length: float) -> float:
