@@ -314,7 +314,17 @@ def use_torch_allocator(enable: bool = True):
 # ---------------------------------------------------------------- solver
 
 class Solver:
-    """One problem on the GPU: create, init, step, read back."""
+    """One problem on the GPU: create, init, step, read back (dvbe_solver_*).
+
+    case: dict with nx, ny, xf[nx+1], yf[ny+1] (face coordinates), RT, tau,
+    dt, scheme ("dugks", "bkg", "cfree_upwind", "cfree_central") and bc, four
+    lists (W, E, S, N) of segments (kind, s0, s1, rho, ux, uy) with kind one
+    of "periodic", "wall", "diffuse", "inflow", "outflow", "outflow_neq",
+    "symmetry".  precision: storage of f_tilde, "f64", "f32", "f32_dev",
+    "f16_dev" or "bf16_dev".  stream: a cudaStream_t (e.g. a torch stream's
+    cuda_stream) or None.  Host arrays are float64 [ny][nx] (fields) or
+    [9][ny][nx] (f_tilde).  Errors raise DvbeError with the library's status.
+    """
 
     def __init__(self, case: dict, precision="f64", stream=None, allow_cfl_ge_1=False,
                  bkg_fd=False, dev_scale=0.0, rho0=1.0):
@@ -439,7 +449,10 @@ class Solver:
 
 
 class Batch:
-    """Many independent cases stepped by one persistent launch per scheme."""
+    """Many independent cases stepped by one persistent launch per scheme
+    (dvbe_batch_*).  cases: case dicts as for Solver (DUGKS or BKG), all with
+    one precision.  A case whose density turns non-finite is flagged
+    (case_status) and skipped from then on; the others continue."""
 
     def __init__(self, cases, precision="f32", allow_cfl_ge_1=False):
         self.cases = cases
