@@ -33,9 +33,9 @@
  *     the mirror point of the first centre.  Corner ghosts: x sides are filled
  *     first (interior rows), then y sides over the full padded width.
  *   - Bounce-back uses the formula of Sec 2.5 literally (no density factor).
- *   - Diffuse wall (parity unpinned apart from zero normal mass flux): the
- *     incoming values are f_eq(rho_w, U_w) with rho_w making the normal mass
- *     flux through the face zero.
+ *   - Diffuse wall (the paper has none): the incoming values are
+ *     f_eq(rho_w, U_w) with rho_w making the normal mass flux through the
+ *     face zero.  Pinned by the Couette slip length.
  *   - Free stream / inflow (Sec 3.3): ghosts are f_eq(rho_inf, U_inf) and,
  *     at the boundary face, the distributions entering the domain are set
  *     to it (those leaving keep their reconstructed values); outflow:

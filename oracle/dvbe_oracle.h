@@ -20,11 +20,15 @@
  *   Sec 3.1  Taylor-Green set-up, Chapman-Enskog initial state, E_u
  *
  * Parity pins for each function are listed in tests/test_oracle_pins.py.
- * Functions without a pin from the paper or from mathematics say
- * "parity unpinned" below:
- *   - the diffuse-reflection wall (the paper has none; only its zero
- *     normal mass flux is pinned),
- *   - the corner-ghost fill order (the paper is silent).
+ * Three rules are readings where the paper is silent; each is pinned by a
+ * consequence derived by hand rather than by the paper:
+ *   - the diffuse-reflection wall: the slip length of plane Couette flow,
+ *     tau c (BKG, the exact DVBE result) and (tau + h/2) c (DUGKS);
+ *   - the free-stream face: the mass that leaves a channel in the first
+ *     step, in closed form, and relaxation to the free stream;
+ *   - the corner-ghost fill order: a box symmetric under a 180-degree
+ *     rotation stays symmetric (this pins the corners against one-sided
+ *     mistakes, not the order itself, which is a convention).
  */
 #ifndef DVBE_ORACLE_H
 #define DVBE_ORACLE_H

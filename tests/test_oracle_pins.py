@@ -381,6 +381,78 @@ def test_set_density_outflow_acts_locally(scheme):
     assert np.max(np.abs(rho1[:, 1:-1] - 1.01)) < 1e-15
 
 
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("rt", [RT, 0.5])
+def test_diffuse_wall_couette_slip_length(scheme, rt):
+    """Diffuse walls (zero normal mass flux, incoming f_eq(rho_w, U_w)) in
+    plane Couette flow.  For the steady DVBE between the walls, f = f_eq(u) -
+    tau xi_y d_y f_eq with u = a + b y is exact to first order in U; at the
+    fixed wall the outgoing D2Q9 directions 7 and 8 carry a shear stress
+    -(c rho / 6)(a + tau c b) and the incoming wall equilibrium none, while
+    the bulk stress is -rho tau c_s^2 b = -rho tau c^2 b / 3.  Equal stress
+    gives the slip a = tau c b: u(y) = U (y + l) / (H + 2 l), slip length
+    l = tau c.  BKG reproduces it exactly (linear fields are reconstructed
+    exactly).  DUGKS applies the wall rule to the face variable
+    f_bar = f - (h/2) Omega, whose non-equilibrium part is (2 tau + h)/(2 tau)
+    times that of f, and its face flux carries 2 tau / (2 tau + h) of it; the
+    same balance gives l = (tau + h/2) c, first order in dt."""
+    case, (r, u, v) = W.couette(4, 16, U=0.05, nu=0.02 * 3 * rt, scheme=scheme, kind="diffuse", RT=rt)
+    n = int(4.0 / case["nu"] / case["dt"])
+    f = O.step(case, O.init_equilibrium(case, r, u, v), n)
+    _, uu, vv = O.moments(case, f)
+    y = W.centres(case["yf"])
+    b, a = np.polyfit(y, uu[:, 0], 1)
+    c, h = math.sqrt(3 * rt), 0.5 * case["dt"]
+    lam = (case["tau"] + (h / 2 if scheme == "dugks" else 0.0)) * c
+    U = case["U"]
+    assert np.max(np.abs(uu - (U * (y + lam) / (1.0 + 2 * lam))[:, None])) < 1e-8 * U
+    assert np.max(np.abs(vv)) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_free_stream_faces_set_entering_directions_only(scheme):
+    """Free-stream faces (Sec 3.3) on W and E at (rho_inf, 0), fluid at rest
+    at rho0 = 1.01 rho_inf, periodic in y.  With the entering directions set
+    to f_eq(rho_inf) and the leaving ones reconstructed between the first
+    cell and the ghost f_eq(rho_inf) (theta = 1/2, normal slope
+    (rho0 - rho_inf) w / dx), each face lets out (c/6)(rho0 - rho_inf)
+    (1/2 + h c / dx) of mass per unit area in the first step, so the excess
+    mass M - rho_inf V falls by the factor 1 - (c dt / (3 Lx))(1/2 + h c / dx).
+    Setting all nine face values would give zero net flux at rest (the mass
+    never relaxes); the reversed selection pushes it away from rho_inf.  Over
+    many steps the domain relaxes to the free stream."""
+    case = W.free_stream_channel(24, scheme)
+    ny, nx = case["ny"], case["nx"]
+    f0 = O.init_equilibrium(case, np.full((ny, nx), 1.01), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    V = (case["xf"][-1] - case["xf"][0]) * (case["yf"][-1] - case["yf"][0])
+    excess = lambda f: O.conserved(case, f)[0] - 1.0 * V
+    e0 = excess(f0)
+    c, dt, dx = 1.0, case["dt"], case["xf"][1] - case["xf"][0]
+    pred = 1.0 - c * dt / (3.0 * 1.0) * (0.5 + 0.5 * dt * c / dx)
+    assert abs(excess(O.step(case, f0, 1)) / e0 - pred) < 1e-12
+    assert abs(excess(O.step(case, f0, 1000)) / e0) < 1e-3
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("kind", ["wall", "diffuse"])
+def test_corner_ghosts_keep_rotation_symmetry(scheme, kind):
+    """Corner ghosts (x sides filled first over the inner rows, then y sides
+    over the padded width, corners included).  A box whose four walls move
+    tangentially in a pattern unchanged by the 180-degree rotation about its
+    centre, on a tanh mesh, started from a rotation-symmetric state: the
+    rotation maps each corner ghost to the opposite one, so the solution must
+    stay symmetric (rho(i, j) = rho(n-1-i, m-1-j), u = -u there) to
+    rounding.  A corner left unfilled, or filled from the wrong side on one
+    side only, breaks it."""
+    case = W.cavity_four_lids(14, 10, scheme=scheme, kind=kind)
+    f = O.step(case, O.init_equilibrium(case, *W.rotation_symmetric_state(case, 9)), 200)
+    r, u, v = O.moments(case, f)
+    R = lambda a: a[::-1, ::-1]
+    assert np.max(np.abs(r - R(r))) < 1e-13
+    assert np.max(np.abs(u + R(u))) < 1e-13 and np.max(np.abs(v + R(v))) < 1e-13
+    assert np.max(np.abs(u)) > 1e-3  # the walls drive a flow
+
+
 # ---------------------------------------------------------------- physics
 
 def test_taylor_green_decay_and_viscosity():
@@ -473,7 +545,25 @@ MUTATIONS = {
     # transposed theta in the y-face blend
     "theta_swap": ("double value = (1.0 - th) * pl + th * pr;\n    double slope_n = (pr - pl) / (yr - yl);",
                    "double value = th * pl + (1.0 - th) * pr;\n    double slope_n = (pr - pl) / (yr - yl);"),
+    # diffuse wall emitting the equilibrium of -U_w
+    "diffuse_uw_sign": ("feq_of(v, 1.0, s->ux, s->uy, f1);", "feq_of(v, 1.0, -s->ux, -s->uy, f1);"),
+    # diffuse wall replacing the outgoing directions instead of the incoming ones
+    "diffuse_select": ("if (xn < 0.0) val[a] = rw * f1[a];", "if (xn > 0.0) val[a] = rw * f1[a];"),
+    # free-stream face setting all nine values (the first reading)
+    "freestream_all_nine": ("if (xn < 0.0) val[a] = fe[a];", "val[a] = fe[a];"),
+    # free-stream face setting the leaving directions
+    "freestream_reversed": ("if (xn < 0.0) val[a] = fe[a];", "if (xn > 0.0) val[a] = fe[a];"),
+    # east corner ghosts never filled
+    "corner_east": ("for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = pg[a];",
+                    "if (i < nx) for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = pg[a];"),
 }
+
+# Mutants of the wall, free-stream and corner rules with the pin written for
+# each.  Those of ONLY_BY_TARGET pass every other pin of the compact set.
+TARGETED = {"diffuse_uw_sign": "diffuse_couette", "diffuse_select": "diffuse_couette",
+            "freestream_all_nine": "free_stream", "freestream_reversed": "free_stream",
+            "corner_east": "corner_symmetry"}
+ONLY_BY_TARGET = {"diffuse_uw_sign", "diffuse_select", "freestream_all_nine", "freestream_reversed"}
 
 
 def _mutant(tmp_path, name):
@@ -513,6 +603,9 @@ def _pins_with(so_path):
             "quadratic_central": lambda: test_quadratic_cell_averages_collisionless("cfree_central"),
             "cfree_identity": lambda: test_upwind_collision_free_face_identity(),
             "outflow_neq": lambda: test_set_density_outflow_acts_locally("dugks"),
+            "diffuse_couette": lambda: test_diffuse_wall_couette_slip_length("dugks", 0.5),
+            "free_stream": lambda: test_free_stream_faces_set_entering_directions_only("bkg"),
+            "corner_symmetry": lambda: test_corner_ghosts_keep_rotation_symmetry("dugks", "wall"),
         }
         for k, fn in checks.items():
             try:
@@ -530,3 +623,7 @@ def _pins_with(so_path):
 def test_planted_mistakes_are_caught(tmp_path, name):
     failed = _pins_with(_mutant(tmp_path, name))
     assert failed, f"mutation {name} passed every pin"
+    if name in TARGETED:
+        assert TARGETED[name] in failed, (name, failed)
+    if name in ONLY_BY_TARGET:
+        assert failed == [TARGETED[name]], (name, failed)

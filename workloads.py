@@ -174,17 +174,55 @@ def cavity(n: int, Re: float = 1000.0, U: float = 0.1, cfl: float = 0.5, scheme:
 
 
 def couette(nx: int, ny: int, U: float = 0.05, nu: float = 0.1, cfl: float = 0.5,
-            scheme: str = "dugks", H: float = 1.0):
-    """Periodic in x; fixed wall at y=0, wall moving at U at y=H; fluid at rest."""
+            scheme: str = "dugks", H: float = 1.0, kind: str = "wall", RT: float = RT_LATTICE):
+    """Periodic in x; fixed wall at y=0, wall moving at U at y=H; fluid at rest.
+    kind: "wall" (bounce-back) or "diffuse"; tau = nu / RT."""
     xf = uniform_faces(nx, 0.0, H * nx / ny)
     yf = uniform_faces(ny, 0.0, H)
-    tau = nu / RT_LATTICE
-    dt = cfl_dt(xf, yf, cfl)
+    tau = nu / RT
+    dt = cfl_dt(xf, yf, cfl, RT)
     per = [("periodic", -INF, INF, 0.0, 0.0, 0.0)]
-    bc = [list(per), list(per), [wall()], [wall(U, 0.0)]]
-    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=bc,
-                nu=nu, U=U, name=f"couette {nx}x{ny}")
+    bc = [list(per), list(per), [wall(kind=kind)], [wall(U, 0.0, kind=kind)]]
+    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT, tau=tau, dt=dt, scheme=scheme, bc=bc,
+                nu=nu, U=U, name=f"couette {nx}x{ny} {kind}")
     return case, (np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+
+
+def cavity_four_lids(nx: int = 14, ny: int = 10, U: float = 0.05, scheme: str = "dugks",
+                     kind: str = "wall", tau: float = 0.01, cfl: float = 0.5, RT: float = RT_LATTICE):
+    """A box whose four walls all move tangentially: S at -U and N at +U in x,
+    W at -0.6 U and E at +0.6 U in y, on a tanh-clustered mesh
+    ([0, 1.4] x [0, 1]).  The problem is unchanged by a rotation through 180
+    degrees about the box centre (x -> Lx - x, y -> Ly - y, u -> -u), which
+    maps each corner to the opposite one."""
+    xf = tanh_faces(nx, 0.0, 1.4, 1.2)
+    yf = tanh_faces(ny, 0.0, 1.0, 1.0)
+    bc = [[wall(0.0, -0.6 * U, kind=kind)], [wall(0.0, 0.6 * U, kind=kind)],
+          [wall(-U, 0.0, kind=kind)], [wall(U, 0.0, kind=kind)]]
+    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=RT, tau=tau, dt=cfl_dt(xf, yf, cfl, RT),
+                scheme=scheme, bc=bc, name=f"four-lid box {nx}x{ny} {kind}")
+    return case
+
+
+def rotation_symmetric_state(case, seed: int, amp_u: float = 0.02, amp_rho: float = 0.01):
+    """Random (rho, ux, uy) unchanged by the 180-degree rotation of the cell
+    grid: rho(i, j) = rho(n-1-i, m-1-j), u(i, j) = -u(n-1-i, m-1-j)."""
+    (r, u, v), _ = random_state(case, seed, amp_u=amp_u, amp_rho=amp_rho)
+    R = lambda a: a[::-1, ::-1]
+    return 0.5 * (r + R(r)), 0.5 * (u - R(u)), 0.5 * (v - R(v))
+
+
+def free_stream_channel(n: int = 24, scheme: str = "dugks", rho_inf: float = 1.0,
+                        tau: float = 0.01, cfl: float = 0.5, RT: float = RT_LATTICE):
+    """[0, 1] x [0, 4/n] periodic in y with free-stream faces on W and E at
+    (rho_inf, 0, 0); the caller chooses the initial state."""
+    xf = uniform_faces(n, 0.0, 1.0)
+    yf = uniform_faces(4, 0.0, 4.0 / n)
+    per = [("periodic", -INF, INF, 0.0, 0.0, 0.0)]
+    fs = [("inflow", -INF, INF, rho_inf, 0.0, 0.0)]
+    return dict(nx=n, ny=4, xf=xf, yf=yf, RT=RT, tau=tau, dt=cfl_dt(xf, yf, cfl, RT),
+                scheme=scheme, bc=[list(fs), list(fs), list(per), list(per)],
+                name=f"free-stream channel {n}x4")
 
 
 def flat_plate(nx_up: int = 40, nx_plate: int = 88, ny: int = 64, U: float = 0.1,
