@@ -28,6 +28,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "symmetry": 5,
          "outflow_neq": 6}
 SCHEMES = {"dugks": 0, "bkg": 1, "cfree_upwind": 2, "cfree_central": 3}
+RECONS = {"linear": 0, "upwind_cell": 1}
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +56,7 @@ class _Problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("xf", _DP), ("yf", _DP),
                 ("RT", ctypes.c_double), ("tau", ctypes.c_double), ("dt", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("nbc", ctypes.c_int * 4),
-                ("bc", ctypes.POINTER(_Seg) * 4)]
+                ("bc", ctypes.POINTER(_Seg) * 4), ("recon", ctypes.c_int)]
 
 
 _lib = None
@@ -103,6 +104,7 @@ class Problem:
         s.xf, s.yf = _dp(self.xf), _dp(self.yf)
         s.RT, s.tau, s.dt = float(case["RT"]), float(case["tau"]), float(case["dt"])
         s.scheme = SCHEMES[case.get("scheme", "dugks")]
+        s.recon = RECONS[case.get("recon", "linear")]
         for side in range(4):
             segs = case["bc"][side]
             arr = (_Seg * len(segs))()

@@ -237,6 +237,7 @@ static int geom_build(const orc_problem *p, geom *g) {
   if (!p || p->nx < 2 || p->ny < 2 || !p->xf || !p->yf) return ORC_EINVAL;
   if (!(p->RT > 0.0) || !(p->tau > 0.0) || !(p->dt > 0.0)) return ORC_EINVAL;
   if (p->scheme < ORC_DUGKS || p->scheme > ORC_CFREE_CENTRAL) return ORC_EINVAL;
+  if (p->recon != ORC_RECON_LINEAR && p->recon != ORC_RECON_UPWIND_CELL) return ORC_EINVAL;
   for (int i = 0; i < p->nx; ++i)
     if (!(p->xf[i + 1] > p->xf[i])) return ORC_EINVAL;
   for (int j = 0; j < p->ny; ++j)
@@ -412,15 +413,55 @@ static void fill_ghosts(const vset *v, const geom *g, double *P) {
 /* Face values                                                        */
 /* ------------------------------------------------------------------ */
 
+/* Cell centre and padded-array column of cell c along x, for c = -2 .. nx+1:
+ * beyond the ghost layer only on a periodic mesh, by the wrap. */
+static double xcell(const geom *g, int c, int *col) {
+  const double Lx = g->xf[g->nx] - g->xf[0];
+  if (c < -1) {
+    *col = c + g->nx;
+    return g->xc[c + g->nx] - Lx;
+  }
+  if (c > g->nx) {
+    *col = c - g->nx;
+    return g->xc[c - g->nx] + Lx;
+  }
+  *col = c;
+  return g->xc[c];
+}
+static double ycell(const geom *g, int c, int *row) {
+  const double Ly = g->yf[g->ny] - g->yf[0];
+  if (c < -1) {
+    *row = c + g->ny;
+    return g->yc[c + g->ny] - Ly;
+  }
+  if (c > g->ny) {
+    *row = c - g->ny;
+    return g->yc[c - g->ny] + Ly;
+  }
+  *row = c;
+  return g->yc[c];
+}
+
 /* phi(x_b - h xi) at the x-face i (between cells i-1 and i), row j. */
 static void recon_xface(const vset *v, const geom *g, const double *P, int i, int j,
-                        double h, double *out) {
+                        double h, int recon, double *out) {
   const size_t plane = (size_t)(g->nx + 2) * (g->ny + 2);
   double xl = g->xc[i - 1], xr = g->xc[i], xb = g->xf[i];
   double th = (xb - xl) / (xr - xl);
   double ylo = g->yc[j - 1], yhi = g->yc[j + 1];
+  const int upwind_ok = recon == ORC_RECON_UPWIND_CELL && (g->per_x || (i > 0 && i < g->nx));
   for (int a = 0; a < 9; ++a) {
     const double *Pa = P + a * plane;
+    if (upwind_ok && v->xi[a][0] != 0.0) {
+      /* upwind cell C and its central differences along x and y */
+      const int C = v->xi[a][0] > 0.0 ? i - 1 : i;
+      int cm, cp, cc;
+      const double xm = xcell(g, C - 1, &cm), xp = xcell(g, C + 1, &cp), xC = xcell(g, C, &cc);
+      const double gx = (Pa[PIDX(g, cp, j)] - Pa[PIDX(g, cm, j)]) / (xp - xm);
+      const double gy = (Pa[PIDX(g, cc, j + 1)] - Pa[PIDX(g, cc, j - 1)]) / (yhi - ylo);
+      out[a] = Pa[PIDX(g, cc, j)] + (xb - h * v->xi[a][0] - xC) * gx - h * v->xi[a][1] * gy;
+      continue;
+    }
     double pl = Pa[PIDX(g, i - 1, j)], pr = Pa[PIDX(g, i, j)];
     double gl = (Pa[PIDX(g, i - 1, j + 1)] - Pa[PIDX(g, i - 1, j - 1)]) / (yhi - ylo);
     double gr = (Pa[PIDX(g, i, j + 1)] - Pa[PIDX(g, i, j - 1)]) / (yhi - ylo);
@@ -433,13 +474,23 @@ static void recon_xface(const vset *v, const geom *g, const double *P, int i, in
 
 /* phi(x_b - h xi) at the y-face j (between rows j-1 and j), column i. */
 static void recon_yface(const vset *v, const geom *g, const double *P, int i, int j,
-                        double h, double *out) {
+                        double h, int recon, double *out) {
   const size_t plane = (size_t)(g->nx + 2) * (g->ny + 2);
   double yl = g->yc[j - 1], yr = g->yc[j], yb = g->yf[j];
   double th = (yb - yl) / (yr - yl);
   double xlo = g->xc[i - 1], xhi = g->xc[i + 1];
+  const int upwind_ok = recon == ORC_RECON_UPWIND_CELL && (g->per_y || (j > 0 && j < g->ny));
   for (int a = 0; a < 9; ++a) {
     const double *Pa = P + a * plane;
+    if (upwind_ok && v->xi[a][1] != 0.0) {
+      const int C = v->xi[a][1] > 0.0 ? j - 1 : j;
+      int rm, rp, rc;
+      const double ym = ycell(g, C - 1, &rm), yp = ycell(g, C + 1, &rp), yC = ycell(g, C, &rc);
+      const double gy = (Pa[PIDX(g, i, rp)] - Pa[PIDX(g, i, rm)]) / (yp - ym);
+      const double gx = (Pa[PIDX(g, i + 1, rc)] - Pa[PIDX(g, i - 1, rc)]) / (xhi - xlo);
+      out[a] = Pa[PIDX(g, i, rc)] + (yb - h * v->xi[a][1] - yC) * gy - h * v->xi[a][0] * gx;
+      continue;
+    }
     double pl = Pa[PIDX(g, i, j - 1)], pr = Pa[PIDX(g, i, j)];
     double gl = (Pa[PIDX(g, i + 1, j - 1)] - Pa[PIDX(g, i - 1, j - 1)]) / (xhi - xlo);
     double gr = (Pa[PIDX(g, i + 1, j)] - Pa[PIDX(g, i - 1, j)]) / (xhi - xlo);
@@ -547,7 +598,7 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
   const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;
   for (int j = 0; j < ny; ++j) {
     for (int i = 0; i <= nx; ++i) {
-      recon_xface(v, g, P, i, j, hs, val);
+      recon_xface(v, g, P, i, j, hs, p->recon, val);
       if (!g->per_x && i == 0) face_bc(v, g->segW[j], -1.0, 0.0, val);
       if (!g->per_x && i == nx) face_bc(v, g->segE[j], 1.0, 0.0, val);
       face_to_f(v, p, val);
@@ -557,7 +608,7 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
   /* y-faces j = 0..ny, columns 0..nx-1 */
   for (int j = 0; j <= ny; ++j) {
     for (int i = 0; i < nx; ++i) {
-      recon_yface(v, g, P, i, j, hs, val);
+      recon_yface(v, g, P, i, j, hs, p->recon, val);
       if (!g->per_y && j == 0) face_bc(v, g->segS[i], 0.0, -1.0, val);
       if (!g->per_y && j == ny) face_bc(v, g->segN[i], 0.0, 1.0, val);
       face_to_f(v, p, val);
@@ -743,13 +794,13 @@ static int implicit_dugks_once(const orc_problem *p, const vset *v, const geom *
   /* Eq. eq_charraw along the characteristic: F - h/2 Omega(F) = f_bar^+(foot) */
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i) {
-      recon_xface(v, g, P, i, j, h, val);
+      recon_xface(v, g, P, i, j, h, p->recon, val);
       if (solve_implicit(v, tau, 0.5 * h, val, F)) return ORC_EINVAL;
       for (int a = 0; a < 9; ++a) FX[(size_t)a * (nx + 1) * ny + (size_t)j * (nx + 1) + i] = F[a];
     }
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {
-      recon_yface(v, g, P, i, j, h, val);
+      recon_yface(v, g, P, i, j, h, p->recon, val);
       if (solve_implicit(v, tau, 0.5 * h, val, F)) return ORC_EINVAL;
       for (int a = 0; a < 9; ++a) FY[(size_t)a * nx * (ny + 1) + (size_t)j * nx + i] = F[a];
     }

@@ -56,6 +56,16 @@ enum {
 
 enum { ORC_SIDE_W = 0, ORC_SIDE_E = 1, ORC_SIDE_S = 2, ORC_SIDE_N = 3 };
 
+/* Reconstruction of the face value phi(x_b - h xi).  ORC_RECON_LINEAR: the
+ * linear interpolation between the two cells of the face (Eqs. eq_char,
+ * f_left).  ORC_RECON_UPWIND_CELL: the alternative of the traditional upwind
+ * FV schemes Sec 2.4 contrasts: the upwind cell C's value carried to the foot
+ * point with C's central-difference gradient, phi_C + (x_b - h xi - x_C) .
+ * grad phi_C.  Directions along the face (xi . n = 0), and faces on a
+ * non-periodic side of the mesh (whose upwind cell would be a ghost), take
+ * the linear reconstruction. */
+enum { ORC_RECON_LINEAR = 0, ORC_RECON_UPWIND_CELL = 1 };
+
 /* One boundary segment on a side: faces whose centre coordinate along the
  * side lies in [s0, s1) take this condition.  (rho, ux, uy) is the wall
  * velocity (walls) or the free-stream state (inflow). */
@@ -76,6 +86,7 @@ typedef struct {
   int scheme;       /* ORC_DUGKS, ORC_BKG, ORC_CFREE_UPWIND or ORC_CFREE_CENTRAL */
   int nbc[4];       /* segments per side, W E S N */
   const orc_bc_segment *bc[4];
+  int recon;        /* ORC_RECON_LINEAR (default) or ORC_RECON_UPWIND_CELL */
 } orc_problem;
 
 /* Status codes: 0 ok, <0 bad argument. */

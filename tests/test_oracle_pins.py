@@ -249,6 +249,104 @@ def test_linear_fields_advect_exactly_on_random_mesh(scheme):
     assert np.max(np.abs(f1[inner] - ex[inner])) < 1e-16
 
 
+# ------------------------------------ upwind-cell reconstruction (Sec 2.4)
+
+def _upwind_case(n, m, scheme, **kw):
+    return dict(periodic_case(n, m, scheme, **kw), recon="upwind_cell")
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_upwind_cell_fourier_factor(scheme):
+    """tau -> infinity, uniform periodic mesh: with the upwind-cell face value
+    phi_C + (x_b - h xi - x_C) . grad phi_C (central-difference gradient of
+    the upwind cell C) each direction is a linear advection scheme.  At the
+    face between cells l and l+1 the value is phi_l A+ when xi > 0 (C = l)
+    and phi_{l+1} A- when xi < 0, with
+      A+ = 1 + (i/2)((1 - n) sin t - n' sin t'),
+      A- = 1 - (i/2)((1 + n) sin t + n' sin t'),
+    n = xi dt / dx along the face normal, n' the other Courant number, t, t'
+    the phase steps; so a Fourier mode is multiplied per step by
+      G = 1 - nx Bx (1 - e^{-i tx}) - ny By (1 - e^{-i ty}),
+    B = A+ or e^{i t} A- by the sign of xi (1-D: Fromm's scheme)."""
+    n, steps = 16, 7
+    case = _upwind_case(n, n, scheme, tau=1e30)
+    dx = 1.0 / n
+    xi, w, _ = O.d2q9(RT)
+    x, y = np.meshgrid(W.centres(case["xf"]), W.centres(case["yf"]))
+    kx, ky = 2 * math.pi * 2, 2 * math.pi * 3
+    tx, ty = kx * dx, ky * dx
+    phase = np.exp(1j * (kx * x + ky * y))
+    f0 = np.array([w[a] * (1.0 + 1e-3 * phase.real) for a in range(9)])
+    f = O.step(case, f0, steps)
+
+    def B(nu, nut, t, tt):
+        if nu > 0:
+            return 1 + 0.5j * ((1 - nu) * math.sin(t) - nut * math.sin(tt))
+        if nu < 0:
+            return np.exp(1j * t) * (1 - 0.5j * ((1 + nu) * math.sin(t) + nut * math.sin(tt)))
+        return 0.0
+
+    for a in range(9):
+        nux, nuy = xi[a] * case["dt"] / dx
+        G = (1 - nux * B(nux, nuy, tx, ty) * (1 - np.exp(-1j * tx))
+             - nuy * B(nuy, nux, ty, tx) * (1 - np.exp(-1j * ty)))
+        ref = w[a] * (1.0 + 1e-3 * (G ** steps * phase).real)
+        assert np.max(np.abs(f[a] - ref)) < 1e-15, a
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_upwind_cell_linear_fields_exact_on_random_mesh(scheme):
+    """Central-difference cell gradients are exact for linear fields on any
+    tensor mesh, so the upwind-cell reconstruction advects a linear field
+    exactly too (collisions off; cells three or more from the seam)."""
+    rng = np.random.default_rng(19)
+    n = 14
+    xf = np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n))]) / n
+    yf = np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n))]) / n
+    case = _upwind_case(n, n, scheme, tau=1e30, xf=xf, yf=yf, dt=W.cfl_dt(xf, yf, 0.4))
+    xi, w, _ = O.d2q9(RT)
+    x, y = np.meshgrid(W.centres(xf), W.centres(yf))
+    gx, gy = 0.7e-2, 1.3e-2
+    f0 = np.array([w[a] * (1 + gx * x + gy * y) for a in range(9)])
+    f1 = O.step(case, f0, 1)
+    dt = case["dt"]
+    ex = np.array([w[a] * (1 + gx * (x - xi[a, 0] * dt) + gy * (y - xi[a, 1] * dt)) for a in range(9)])
+    inner = (slice(None), slice(3, n - 3), slice(3, n - 3))
+    assert np.max(np.abs(f1[inner] - ex[inner])) < 1e-16
+    # and it is not the linear-interpolation face: the two differ on a curved field
+    fq = np.array([w[a] * (1 + 0.1 * np.sin(6 * x) * np.cos(5 * y)) for a in range(9)])
+    assert np.max(np.abs(O.step(case, fq, 1) - O.step(dict(case, recon="linear"), fq, 1))) > 1e-6
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("stretched", [False, True])
+def test_upwind_cell_fixed_point_and_conservation(scheme, stretched):
+    """Uniform flow stays exactly in place; mass and momentum are exact on a
+    periodic mesh (the flux through a face is one value for both cells)."""
+    xf = W.tanh_faces(12, 0.0, 1.0, 1.2) if stretched else None
+    case = _upwind_case(12, 10, scheme, tau=0.02, xf=xf)
+    f0 = O.init_equilibrium(case, np.full((10, 12), 1.01), np.full((10, 12), 0.03),
+                            np.full((10, 12), -0.02))
+    assert np.max(np.abs(O.step(case, f0, 20) - f0)) < 2e-16 * 20
+    (r, u, v), delta = W.random_state(case, 3, amp_neq=1e-3)
+    g0 = O.init_equilibrium(case, r, u, v) + delta
+    c0, c1 = O.conserved(case, g0), O.conserved(case, O.step(case, g0, 30))
+    assert abs(c1[0] - c0[0]) < 1e-14 * abs(c0[0])
+    assert np.max(np.abs(c1[1:] - c0[1:])) < 1e-14 * abs(c0[0])
+
+
+def test_upwind_cell_walls_use_linear_faces():
+    """On a non-periodic side the face's upwind cell would be a ghost: such
+    faces take the linear reconstruction, so a closed cavity conserves mass
+    exactly and a Couette flow is linear, as with the default."""
+    case, _ = W.couette(4, 16, U=0.05, nu=0.1, scheme="dugks")
+    case = dict(case, recon="upwind_cell")
+    n = int(3.0 / case["nu"] / case["dt"])
+    f = O.step(case, O.init_equilibrium(case, np.ones((16, 4)), np.zeros((16, 4)), np.zeros((16, 4))), n)
+    _, uu, _ = O.moments(case, f)
+    assert np.max(np.abs(uu - case["U"] * W.centres(case["yf"])[:, None])) < 1e-7 * case["U"]
+
+
 # ------------------------------------------- collision-free faces (Sec 2.4)
 
 @pytest.mark.parametrize("scheme", ALL_SCHEMES)
@@ -553,6 +651,11 @@ MUTATIONS = {
     "freestream_all_nine": ("if (xn < 0.0) val[a] = fe[a];", "val[a] = fe[a];"),
     # free-stream face setting the leaving directions
     "freestream_reversed": ("if (xn < 0.0) val[a] = fe[a];", "if (xn > 0.0) val[a] = fe[a];"),
+    # upwind-cell reconstruction taking the downwind cell
+    "upwind_cell_side": ("const int C = v->xi[a][0] > 0.0 ? i - 1 : i;", "const int C = v->xi[a][0] > 0.0 ? i : i - 1;"),
+    # upwind-cell reconstruction without its tangential term
+    "upwind_cell_tangential": ("out[a] = Pa[PIDX(g, cc, j)] + (xb - h * v->xi[a][0] - xC) * gx - h * v->xi[a][1] * gy;",
+                               "out[a] = Pa[PIDX(g, cc, j)] + (xb - h * v->xi[a][0] - xC) * gx;"),
     # east corner ghosts never filled
     "corner_east": ("for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = pg[a];",
                     "if (i < nx) for (int a = 0; a < 9; ++a) P[a * plane + PIDX(g, i, jg)] = pg[a];"),
@@ -562,8 +665,10 @@ MUTATIONS = {
 # each.  Those of ONLY_BY_TARGET pass every other pin of the compact set.
 TARGETED = {"diffuse_uw_sign": "diffuse_couette", "diffuse_select": "diffuse_couette",
             "freestream_all_nine": "free_stream", "freestream_reversed": "free_stream",
-            "corner_east": "corner_symmetry"}
-ONLY_BY_TARGET = {"diffuse_uw_sign", "diffuse_select", "freestream_all_nine", "freestream_reversed"}
+            "corner_east": "corner_symmetry", "upwind_cell_side": "upwind_cell_fourier",
+            "upwind_cell_tangential": "upwind_cell_fourier"}
+ONLY_BY_TARGET = {"diffuse_uw_sign", "diffuse_select", "freestream_all_nine", "freestream_reversed",
+                  "upwind_cell_side", "upwind_cell_tangential"}
 
 
 def _mutant(tmp_path, name):
@@ -606,6 +711,7 @@ def _pins_with(so_path):
             "diffuse_couette": lambda: test_diffuse_wall_couette_slip_length("dugks", 0.5),
             "free_stream": lambda: test_free_stream_faces_set_entering_directions_only("bkg"),
             "corner_symmetry": lambda: test_corner_ghosts_keep_rotation_symmetry("dugks", "wall"),
+            "upwind_cell_fourier": lambda: test_upwind_cell_fourier_factor("dugks"),
         }
         for k, fn in checks.items():
             try:
