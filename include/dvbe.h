@@ -122,7 +122,27 @@ typedef struct {
                        BF16); ignored otherwise (F32_DEV stores d unscaled)     */
   void *cuda_stream; /* cudaStream_t to run on (NULL: the library creates its own
                         non-blocking stream)                                    */
+  int recon;        /* dvbe_recon: face reconstruction (0: linear)               */
+  int path;         /* dvbe_path: 0 the fused step kernels where they apply,
+                       1 the multi-pass step with face arrays                   */
 } dvbe_params;
+
+/* Reconstruction of the face value phi(x_b - h xi).  DVBE_RECON_LINEAR: the
+ * linear interpolation between the two cells of the face (Eqs. eq_char,
+ * f_left), the paper's.  DVBE_RECON_UPWIND_CELL: the reconstruction of the
+ * traditional upwind FV schemes Sec 2.4 contrasts with it: the upwind cell
+ * C's value carried to the foot point with C's central-difference gradient,
+ * phi_C + (x_b - h xi - x_C) . grad phi_C; directions along a face, and faces
+ * on non-periodic sides, keep the linear one.  It runs on the multi-pass
+ * path (FP64), single solver only. */
+typedef enum { DVBE_RECON_LINEAR = 0, DVBE_RECON_UPWIND_CELL = 1 } dvbe_recon;
+
+/* Step implementation.  DVBE_PATH_FUSED: one fused kernel (two on meshes
+ * with inner strips) per step, every precision.  DVBE_PATH_MULTIPASS: the
+ * step as separate kernels with face arrays in device memory (cell stage,
+ * ghost layers, x faces, y faces, update; about five times the memory traffic
+ * of the fused step), FP64 only; it carries the reconstruction variants. */
+typedef enum { DVBE_PATH_FUSED = 0, DVBE_PATH_MULTIPASS = 1 } dvbe_path;
 
 /* ---- velocity set and mesh --------------------------------------------- */
 
@@ -218,15 +238,69 @@ DVBE_API dvbe_status dvbe_get_launch(dvbe_solver s, dvbe_launch *out);
 DVBE_API dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in);
 /* Time each candidate launch shape on this solver's own state for `steps`
  * steps and keep the fastest; the state is restored afterwards.  best_ms
- * (may be NULL) receives the fastest time per step. */
+ * (may be NULL) receives the fastest time per step.  Candidates: strip
+ * heights from 8 to 256 rows and the heights that make the inner strips fill
+ * a whole number of waves of resident warps, with 2, 4 or 8 warps per block,
+ * each with a grid of one block per strip group or one wave of blocks.  The
+ * choice is cached (dvbe_set_autotune_cache) under the scheme, precision,
+ * mesh size and periodicity, GPU model and library build: a later call with
+ * the same key takes the cached shape without timing anything. */
 DVBE_API dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms);
+/* Autotuner cache file (JSON).  NULL: no cache; "": the default, which is
+ * $DVBE_AUTOTUNE_CACHE if set (empty: no cache), else
+ * $XDG_CACHE_HOME/dvbe/autotune.json, else $HOME/.cache/dvbe/autotune.json.
+ * Process-wide. */
+DVBE_API dvbe_status dvbe_set_autotune_cache(const char *path);
 
 /* Device view of the current f_tilde (for timing and inspection): base
  * pointer, row pitch in elements, elements per field, element size. */
 DVBE_API dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch,
                               long long *plane, int *elem_bytes);
-/* Kernel launches issued since creation (every step kernel, init, reduction). */
+/* Kernel launches issued since creation (every step kernel, init, reduction).
+ * A step is one launch, or two on meshes with inner strips: the strips that
+ * touch no boundary run in a kernel compiled without boundary code. */
 DVBE_API dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
+
+/* Spatial decomposition (the paper has none; its FV form on cells V_k and
+ * their faces, Sec 2.2, is what lets a mesh be split into blocks).  One
+ * line of cells of all nine fields moved between the solver's f_tilde and a
+ * dense device buffer [9][hi-lo] of the solver's storage element (values as
+ * stored): axis 0 is column `index` over rows lo..hi-1, axis 1 row `index`
+ * over columns lo..hi-1.  Used to exchange the halo ring of a block with its
+ * neighbours between steps.  The calls wait for the copy.  A line outside
+ * the mesh: DVBE_ERR_INVALID_ARG. */
+DVBE_API dvbe_status dvbe_pack_line(dvbe_solver s, int axis, int index, int lo, int hi, void *dev_buf);
+DVBE_API dvbe_status dvbe_unpack_line(dvbe_solver s, int axis, int index, int lo, int hi,
+                                      const void *dev_buf);
+/* dvbe_conserved over the window of cells [i0, i0+nx) x [j0, j0+ny) (FP64,
+ * deterministic order): the owned cells of a block. */
+DVBE_API dvbe_status dvbe_conserved_window(dvbe_solver s, int i0, int j0, int nx, int ny, double out[3]);
+
+/* Checkpoint and restart (the paper has no counterpart).  The device storage
+ * of f_tilde exactly as stored ([9][ny][pitch] elements of the solver's
+ * precision, padding included), so a solver of the same problem restarted
+ * from it continues bit for bit, whatever the storage mode (dvbe_get_f /
+ * dvbe_init_f round-trip exactly only for DVBE_F64 and DVBE_F32).
+ * dvbe_state_bytes gives the size; save copies it to host memory the caller
+ * owns (and the step count to *step, may be NULL); load copies it back and
+ * sets the step count.  A buffer of another size: DVBE_ERR_INVALID_ARG. */
+DVBE_API dvbe_status dvbe_state_bytes(dvbe_solver s, size_t *bytes);
+DVBE_API dvbe_status dvbe_save_state(dvbe_solver s, void *host, size_t bytes, long long *step);
+DVBE_API dvbe_status dvbe_load_state(dvbe_solver s, const void *host, size_t bytes, long long step);
+
+/* Failure detection of the step kernel (the paper has no counterpart).  Each
+ * warp stages rows through asynchronous copies completed on mbarriers; a copy
+ * not complete at its first test is polled at most `polls` more times, after
+ * which the warp stops fetching, waits (bounded) for the copies it has in
+ * flight, and leaves; the step then returns DVBE_ERR_TIMEOUT and the state is
+ * not a valid time level (re-initialise it).  The default is
+ * DVBE_DEFAULT_WAIT_LIMIT polls, and every wait also gives up after about a
+ * second of SM clock cycles, far longer than any copy takes.  0 serves tests
+ * of the failure path: every wait gives up at once, so each warp stops at
+ * its first fetch.  polls < 0: DVBE_ERR_INVALID_ARG.  Waits for queued work
+ * first. */
+#define DVBE_DEFAULT_WAIT_LIMIT 16777216LL
+DVBE_API dvbe_status dvbe_set_wait_limit(dvbe_solver s, long long polls);
 
 /* Allocation-free variant of dvbe_conserved.  The paper has no counterpart:
  * this is an interface for callers that cannot allocate device memory, such as
@@ -272,6 +346,9 @@ DVBE_API dvbe_status dvbe_batch_get_f(dvbe_batch b, int icase, double *f_tilde);
 DVBE_API dvbe_status dvbe_batch_set_launch(dvbe_batch b, const dvbe_launch *in);
 DVBE_API dvbe_status dvbe_batch_autotune(dvbe_batch b, int steps, double *best_ms);
 DVBE_API dvbe_status dvbe_batch_launch_count(dvbe_batch b, long long *count);
+/* dvbe_set_wait_limit for every case of a batch; a case whose wait ran out
+ * reports DVBE_ERR_TIMEOUT from dvbe_batch_case_status. */
+DVBE_API dvbe_status dvbe_batch_set_wait_limit(dvbe_batch b, long long polls);
 
 /* ---- misc --------------------------------------------------------------- */
 

@@ -31,12 +31,15 @@ KINDS = {"periodic": 0, "wall": 1, "diffuse": 2, "inflow": 3, "outflow": 4, "sym
          "outflow_neq": 6}
 SCHEMES = {"dugks": 0, "bkg": 1, "cfree_upwind": 2, "cfree_central": 3}
 PRECISIONS = {"f64": 0, "f32": 1, "f32_dev": 2, "f16_dev": 3, "bf16_dev": 4}
+RECONS = {"linear": 0, "upwind_cell": 1}
+PATHS = {"fused": 0, "multipass": 1}
 STATUS = {0: "DVBE_OK", 1: "DVBE_ERR_INVALID_ARG", 2: "DVBE_ERR_CFL", 3: "DVBE_ERR_OOM",
           4: "DVBE_ERR_CUDA", 5: "DVBE_ERR_DIVERGED", 6: "DVBE_ERR_TIMEOUT",
           7: "DVBE_ERR_UNSUPPORTED"}
 DVBE_OK, DVBE_ERR_INVALID_ARG, DVBE_ERR_CFL, DVBE_ERR_OOM = 0, 1, 2, 3
 DVBE_ERR_CUDA, DVBE_ERR_DIVERGED, DVBE_ERR_TIMEOUT, DVBE_ERR_UNSUPPORTED = 4, 5, 6, 7
 
+DEFAULT_WAIT_LIMIT = 16777216  # DVBE_DEFAULT_WAIT_LIMIT
 _DP = ctypes.POINTER(ctypes.c_double)
 
 
@@ -51,7 +54,7 @@ class dvbe_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("bc", ctypes.POINTER(dvbe_bc_segment) * 4),
                 ("nbc", ctypes.c_int * 4), ("allow_cfl_ge_1", ctypes.c_int),
                 ("bkg_fd", ctypes.c_int), ("dev_scale", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("recon", ctypes.c_int), ("path", ctypes.c_int)]
 
 
 class dvbe_launch(ctypes.Structure):
@@ -94,10 +97,22 @@ _SIGS = {
     "dvbe_get_launch": [ctypes.c_void_p, ctypes.POINTER(dvbe_launch)],
     "dvbe_set_launch": [ctypes.c_void_p, ctypes.POINTER(dvbe_launch)],
     "dvbe_autotune": [ctypes.c_void_p, ctypes.c_int, _DP],
+    "dvbe_set_autotune_cache": [ctypes.c_char_p],
     "dvbe_device_state": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                           ctypes.POINTER(ctypes.c_int)],
     "dvbe_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "dvbe_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
+    "dvbe_state_bytes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+    "dvbe_pack_line": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_void_p],
+    "dvbe_unpack_line": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                         ctypes.c_void_p],
+    "dvbe_conserved_window": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              _DP],
+    "dvbe_save_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                        ctypes.POINTER(ctypes.c_longlong)],
+    "dvbe_load_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_longlong],
     "dvbe_batch_create": [ctypes.POINTER(dvbe_params), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
     "dvbe_batch_destroy": [ctypes.c_void_p],
     "dvbe_batch_init_equilibrium": [ctypes.c_void_p, ctypes.c_int, _DP, _DP, _DP],
@@ -108,6 +123,7 @@ _SIGS = {
     "dvbe_batch_set_launch": [ctypes.c_void_p, ctypes.POINTER(dvbe_launch)],
     "dvbe_batch_autotune": [ctypes.c_void_p, ctypes.c_int, _DP],
     "dvbe_batch_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "dvbe_batch_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
     "dvbe_conserved_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p],
@@ -221,7 +237,7 @@ def dvbe_dt_from_cfl(mesh, RT, cfl):
 # ---------------------------------------------------------------- parameters
 
 def make_params(case: dict, mesh, precision="f64", stream=None, allow_cfl_ge_1=False,
-                bkg_fd=False, dev_scale=0.0, rho0=1.0):
+                bkg_fd=False, dev_scale=0.0, rho0=1.0, path="fused"):
     """dvbe_params for a case dict; returns (params, keep-alive list)."""
     p = dvbe_params()
     p.mesh = mesh
@@ -244,6 +260,8 @@ def make_params(case: dict, mesh, precision="f64", stream=None, allow_cfl_ge_1=F
     p.bkg_fd = int(bool(bkg_fd))
     p.dev_scale = float(dev_scale)
     p.cuda_stream = stream if stream is None else ctypes.c_void_p(int(stream))
+    p.recon = RECONS[case.get("recon", "linear")]
+    p.path = PATHS[path]
     return p, keep
 
 
@@ -256,6 +274,11 @@ def dvbe_conserved_noalloc(f_tilde_ptr, precision, nx, ny, pitch, dx_ptr, dy_ptr
           int(pitch), ctypes.c_void_p(dx_ptr), ctypes.c_void_p(dy_ptr), float(RT), float(rho0),
           float(dev_scale), ctypes.c_void_p(out_ptr),
           None if stream is None else ctypes.c_void_p(int(stream)))
+
+
+def dvbe_set_autotune_cache(path):
+    """Autotuner cache file: a path, "" for the default, None for no cache."""
+    _call("dvbe_set_autotune_cache", None if path is None else os.fsencode(path))
 
 
 def dvbe_solver_create(params):
@@ -317,24 +340,26 @@ class Solver:
     """One problem on the GPU: create, init, step, read back (dvbe_solver_*).
 
     case: dict with nx, ny, xf[nx+1], yf[ny+1] (face coordinates), RT, tau,
-    dt, scheme ("dugks", "bkg", "cfree_upwind", "cfree_central") and bc, four
+    dt, scheme ("dugks", "bkg", "cfree_upwind", "cfree_central"), optionally
+    recon ("linear" or "upwind_cell", the latter on the multi-pass path), and bc, four
     lists (W, E, S, N) of segments (kind, s0, s1, rho, ux, uy) with kind one
     of "periodic", "wall", "diffuse", "inflow", "outflow", "outflow_neq",
     "symmetry".  precision: storage of f_tilde, "f64", "f32", "f32_dev",
-    "f16_dev" or "bf16_dev".  stream: a cudaStream_t (e.g. a torch stream's
+    "f16_dev" or "bf16_dev".  path: "fused" (default) or "multipass" (FP64,
+    face arrays in device memory).  stream: a cudaStream_t (e.g. a torch stream's
     cuda_stream) or None.  Host arrays are float64 [ny][nx] (fields) or
     [9][ny][nx] (f_tilde).  Errors raise DvbeError with the library's status.
     """
 
     def __init__(self, case: dict, precision="f64", stream=None, allow_cfl_ge_1=False,
-                 bkg_fd=False, dev_scale=0.0, rho0=1.0):
+                 bkg_fd=False, dev_scale=0.0, rho0=1.0, path="fused"):
         self.case = case
         self.nx, self.ny = int(case["nx"]), int(case["ny"])
         self.precision = precision
         mesh = dvbe_mesh_create(case["xf"], case["yf"])
         try:
             params, keep = make_params(case, mesh, precision, stream, allow_cfl_ge_1, bkg_fd,
-                                       dev_scale, rho0)
+                                       dev_scale, rho0, path)
             self.h = dvbe_solver_create(params)
         finally:
             dvbe_mesh_destroy(mesh)
@@ -447,6 +472,37 @@ class Solver:
         _call("dvbe_launch_count", self.h, ctypes.byref(n))
         return n.value
 
+    def pack_line(self, axis, index, lo, hi, dev_ptr):
+        """One line of cells of all nine fields into a device buffer [9][hi-lo]
+        (axis 0: column `index` over rows lo..hi-1; axis 1: a row)."""
+        _call("dvbe_pack_line", self.h, int(axis), int(index), int(lo), int(hi), ctypes.c_void_p(dev_ptr))
+
+    def unpack_line(self, axis, index, lo, hi, dev_ptr):
+        _call("dvbe_unpack_line", self.h, int(axis), int(index), int(lo), int(hi), ctypes.c_void_p(dev_ptr))
+
+    def conserved_window(self, i0, j0, nx, ny):
+        out = np.zeros(3)
+        _call("dvbe_conserved_window", self.h, int(i0), int(j0), int(nx), int(ny), _dp(out))
+        return out
+
+    def save_state(self):
+        """Checkpoint: (raw device storage of f_tilde as bytes, step count)."""
+        n = ctypes.c_size_t()
+        _call("dvbe_state_bytes", self.h, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        step = ctypes.c_longlong()
+        _call("dvbe_save_state", self.h, buf, n.value, ctypes.byref(step))
+        return buf.raw, step.value
+
+    def load_state(self, state: bytes, step: int = 0):
+        """Restart from a checkpoint of save_state (same problem and precision)."""
+        _call("dvbe_load_state", self.h, state, len(state), int(step))
+
+    def set_wait_limit(self, polls: int = None):
+        """Polls of a pending row copy before a step gives up with
+        DVBE_ERR_TIMEOUT (None: the library default)."""
+        _call("dvbe_set_wait_limit", self.h, DEFAULT_WAIT_LIMIT if polls is None else int(polls))
+
 
 class Batch:
     """Many independent cases stepped by one persistent launch per scheme
@@ -519,3 +575,6 @@ class Batch:
         n = ctypes.c_longlong()
         _call("dvbe_batch_launch_count", self.h, ctypes.byref(n))
         return n.value
+
+    def set_wait_limit(self, polls: int = None):
+        _call("dvbe_batch_set_wait_limit", self.h, DEFAULT_WAIT_LIMIT if polls is None else int(polls))

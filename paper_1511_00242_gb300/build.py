@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdvbe.so")
 SOURCES = ["step_f64.cu", "step_f32.cu", "step_f16.cu", "aux_kernels.cu", "dvbe_capi.cu", "batch.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "tune_cache.cu", "multipass.cu"]
 HEADERS = ["internal.h", "capi_common.h", "step_kernel.cuh"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -40,7 +40,21 @@ def _stale(target: str, deps) -> bool:
 
 
 KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL",
-         "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL", "DVBE_STAGES")
+         "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL", "DVBE_STAGES",
+         "DVBE_PAIR_INNER_MAXREG", "DVBE_RING_CONCURRENT", "DVBE_RING_FIRST", "DVBE_RING_PRIORITY")
+
+
+def _build_id(extra):
+    """Hash of the sources, headers and knobs: names the build in the
+    autotuner cache, so a changed kernel never reuses an old choice."""
+    import hashlib
+    h = hashlib.sha256(" ".join(NVCC_FLAGS + extra).encode())
+    for name in sorted(SOURCES + HEADERS):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(ROOT, "include", "dvbe.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _flags():
@@ -59,13 +73,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         force = True
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "dvbe.h")]
     objs, jobs = [], []
+    extra = [f for f in _flags() if f not in NVCC_FLAGS]
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc()] + _flags() + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
-            jobs.append(cmd)
+        # the cache unit carries the build id, which depends on every source
+        deps = [os.path.join(CSRC, x) for x in SOURCES] if src == "tune_cache.cu" else [s]
+        if force or _stale(o, deps + hdrs):
+            cmd = [nvcc()] + _flags() + (["-Xptxas", "-v"] if ptxas_info else [])
+            if src == "tune_cache.cu":
+                cmd.append('-DDVBE_BUILD_ID="%s"' % _build_id(extra))
+            jobs.append(cmd + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

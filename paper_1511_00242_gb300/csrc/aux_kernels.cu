@@ -256,6 +256,30 @@ __global__ void k_finish3(const double *partials, int nblocks, double *out) {
   }
 }
 
+// One line of cells of all nine fields copied between the f_tilde storage
+// and a dense buffer [9][n] of the same element type (es bytes): axis 0 is
+// column `index` over rows lo .. lo+n-1, axis 1 row `index` over columns
+// lo .. lo+n-1; to_buf selects the direction.  Values are moved as stored.
+__global__ void k_copy_line(FieldView v, int es, int axis, int index, int lo, int n, char *buf,
+                            int to_buf) {
+  const long long total = 9LL * n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(k / n), p = lo + (int)(k % n);
+    const long long idx = axis == 0 ? (long long)p * v.pitch + index : (long long)index * v.pitch + p;
+    char *cell = (char *)v.f + (a * v.plane + idx) * es;
+    char *b = buf + k * es;
+    char *dst = to_buf ? b : cell;
+    const char *src = to_buf ? cell : b;
+    if (es == 8)
+      *(unsigned long long *)dst = *(const unsigned long long *)src;
+    else if (es == 4)
+      *(unsigned *)dst = *(const unsigned *)src;
+    else
+      *(unsigned short *)dst = *(const unsigned short *)src;
+  }
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g > 4096) g = 4096;
@@ -302,6 +326,12 @@ cudaError_t aux_conserved(const FieldView &v, const double *volx, const double *
                           double *partials, double *out, cudaStream_t s) {
   k_conserved<<<kReduceBlocks, kRT, 0, s>>>(v, volx, voly, partials);
   k_finish3<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t aux_copy_line(const FieldView &v, int elem, int axis, int index, int lo, int n,
+                          void *buf, int to_buf, cudaStream_t s) {
+  k_copy_line<<<grid_for(9LL * n), 256, 0, s>>>(v, elem, axis, index, lo, n, (char *)buf, to_buf);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 // others are unaffected.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -145,6 +146,8 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
       st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs BKG in finite-volume form only");
     if (st == DVBE_OK && b->pb[c].kernel == SC_CFREE)
       st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs DUGKS and BKG only");
+    if (st == DVBE_OK && b->pb[c].multipass)
+      st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs the fused step with the linear reconstruction");
     if (st == DVBE_OK && c > 0 && b->pb[c].store != b->pb[0].store)
       st = fail(DVBE_ERR_INVALID_ARG, "all cases of a batch must share one precision");
     if (st == DVBE_OK) st = upload_problem(b->pb[c], b->dp[c], b->args[c], b->stream);
@@ -319,8 +322,40 @@ dvbe_status dvbe_batch_set_launch(dvbe_batch b, const dvbe_launch *in) {
   return batch_tables(b);
 }
 
+// Cache key of a batch: storage mode, case count and a hash (FNV-1a) of
+// every case's kernel, mesh size and periodicity.
+static std::string batch_tune_key(dvbe_batch b) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](long long v) {
+    for (int k = 0; k < 8; ++k) {
+      h ^= (unsigned long long)((v >> (8 * k)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  for (int c = 0; c < b->n; ++c) {
+    mix(b->pb[c].kernel);
+    mix(b->pb[c].nx);
+    mix(b->pb[c].ny);
+    mix(b->pb[c].per_x * 2 + b->pb[c].per_y);
+  }
+  char s[160];
+  snprintf(s, sizeof s, "k_step_batch|store %d|%d cases|%016llx", b->store, b->n, h);
+  return tune_key(s);
+}
+
 dvbe_status dvbe_batch_autotune(dvbe_batch b, int steps, double *best_ms) {
   if (!b || steps < 1) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  const std::string key = batch_tune_key(b);
+  TuneEntry hit;
+  if (tune_lookup(key, &hit) && hit.strip_rows >= 1 && hit.warps_per_block >= 1 &&
+      hit.warps_per_block <= 8 && hit.blocks >= 0) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+    b->launch = {hit.strip_rows, hit.warps_per_block, hit.blocks, 0};
+    batch_drop_graphs(b);
+    if (best_ms) *best_ms = hit.ms;
+    return batch_tables(b);
+  }
   // back up the current state of every case
   size_t total = 0;
   std::vector<size_t> bytes(b->n);
@@ -392,8 +427,23 @@ dvbe_status dvbe_batch_autotune(dvbe_batch b, int steps, double *best_ms) {
   dvbe_status st = batch_tables(b);
   if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
   if (st != DVBE_OK) return st;
+  TuneEntry te;
+  te.strip_rows = bestc.strip_rows;
+  te.warps_per_block = bestc.warps_per_block;
+  te.blocks = bestc.blocks;
+  te.ms = best;
+  tune_store(key, te);
   if (best_ms) *best_ms = best;
   return DVBE_OK;
+}
+
+dvbe_status dvbe_batch_set_wait_limit(dvbe_batch b, long long polls) {
+  if (!b || polls < 0) return fail(DVBE_ERR_INVALID_ARG, "NULL batch or negative poll count");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch set_wait_limit");
+  for (auto &a : b->args) a.wait_limit = (unsigned long long)polls;
+  batch_drop_graphs(b);
+  return batch_tables(b);
 }
 
 dvbe_status dvbe_batch_launch_count(dvbe_batch b, long long *count) {

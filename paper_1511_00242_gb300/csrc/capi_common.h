@@ -26,6 +26,10 @@ struct Problem {
   double ext[4] = {0, 0, 0, 0};
   std::vector<unsigned char> segid[4];
   double b_phi = 0, q_face = 0, fd_nux = 0, fd_nuy = 0; // transform coefficients (increment forms)
+  double b_tp = 0;             // f_tilde^+ = f_tilde + b_tp (f_eq - f_tilde)
+  int recon = 0;               // dvbe_recon
+  bool multipass = false;      // multi-pass FP64 step with face arrays
+  std::vector<double> xg, yg, xoff, yoff; // its gradient and foot-offset tables (MPArgs)
   int pitch = 0, elem = 0;
   long long plane = 0;
 };
@@ -36,6 +40,33 @@ struct DeviceProblem {
   double *volx = nullptr, *voly = nullptr;
 };
 
+// Buffers and tables of the multi-pass FP64 step (multipass.cu).
+struct MPArgs {
+  double *phi;         // [9][ny+4][nx+4]: phi with two ghost layers
+  long long pplane;    // (ny+4)(nx+4)
+  double *tp;          // [9][ny][nx]: f_tilde^+
+  double *fx, *fy;     // [9][ny][nx+1], [9][ny+1][nx]: face distributions
+  const double *xg;    // [nx+4]: cell c at c+2: h c / (x_{c+1} - x_{c-1})
+  const double *yg;    // [ny+4]
+  const double *xoff;  // [2(nx+1)]: face k: (x_b - x_{k-1}) / (h c), (x_b - x_k) / (h c)
+  const double *yoff;  // [2(ny+1)]
+  double b_tp;         // f_tilde^+ = f_tilde + b_tp (f_eq - f_tilde)
+  int nx, ny, recon, scheme;
+};
+cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s);
+constexpr int kMultipassKernels = 6; // launches of one multi-pass step
+
+// Autotuner cache (tune_cache.cu): launch shapes keyed by tune_key(what),
+// which appends the GPU name, SM count and library build to `what`.
+struct TuneEntry {
+  int strip_rows = 0, warps_per_block = 0, blocks = 0;
+  double ms = 0;
+};
+void tune_set_path(const char *path);
+std::string tune_key(const std::string &what);
+bool tune_lookup(const std::string &key, TuneEntry *out);
+void tune_store(const std::string &key, const TuneEntry &e);
+
 dvbe_status fail(dvbe_status st, const std::string &msg);
 dvbe_status cuda_fail(cudaError_t e, const char *what);
 void *dmalloc(size_t bytes, cudaStream_t s);
@@ -43,6 +74,8 @@ void dfree(void *p, cudaStream_t s);
 dvbe_status build_problem(const dvbe_params *p, Problem &pb);
 dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cudaStream_t s);
 void set_strips(CaseArgs &a, int H, int store);
+// Kernel launches of one step (two when the inner strips run in their own kernel).
+int kernels_per_step(const CaseArgs &a);
 FieldView view_of(const Problem &pb, void *f);
 int sm_count();
 dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStream_t s,
@@ -51,11 +84,14 @@ dvbe_status stage_fields(const double *const *src, int count, size_t n, cudaStre
 dvbe_status make_tensor_maps(const Problem &pb, void *f, CUtensorMap *main_map,
                              CUtensorMap *wrap_map);
 
-cudaError_t launch_step_f64(int scheme, const CaseArgs &a, int blocks, int wpb, cudaStream_t s);
+cudaError_t launch_step_f64(int scheme, const CaseArgs &a, int blocks, int wpb, const StepStreams &s);
 cudaError_t launch_step_f32(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
-                            cudaStream_t s);
+                            const StepStreams &s);
 cudaError_t launch_step_f16(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
-                            cudaStream_t s);
+                            const StepStreams &s);
+int inner_blocks_per_sm_f64(int scheme, int wpb);
+int inner_blocks_per_sm_f32(int store, int scheme, int wpb);
+int inner_blocks_per_sm_f16(int store, int scheme, int wpb);
 cudaError_t launch_batch_f64(int scheme, const CaseArgs *c, const long long *p, int n, long long ni,
                              unsigned long long *q, int blocks, int wpb, cudaStream_t s);
 cudaError_t launch_batch_f32(int store, int scheme, const CaseArgs *c, const long long *p, int n,

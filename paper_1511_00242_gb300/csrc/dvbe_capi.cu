@@ -13,6 +13,10 @@
 
 using namespace dvbe;
 
+#ifndef DVBE_RING_PRIORITY
+#define DVBE_RING_PRIORITY 0
+#endif
+
 // ---------------------------------------------------------------------------
 // errors, allocator
 // ---------------------------------------------------------------------------
@@ -53,7 +57,7 @@ void dfree(void *p, cudaStream_t s) {
 }
 
 cudaError_t launch_step(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
-                        cudaStream_t s) {
+                        const StepStreams &s) {
   switch (store) {
     case ST_F64:
       return launch_step_f64(scheme, a, blocks, wpb, s);
@@ -111,6 +115,8 @@ static int find_seg(const std::vector<dvbe_bc_segment> &segs, double t) {
   return -1;
 }
 
+static double c_lat(const Problem &pb) { return std::sqrt(3.0 * pb.RT); }
+
 dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   if (!p) return fail(DVBE_ERR_INVALID_ARG, "params is NULL");
   if (!p->mesh) return fail(DVBE_ERR_INVALID_ARG, "params.mesh is NULL");
@@ -167,6 +173,17 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   }
 
   pb.kernel = p->scheme == DVBE_DUGKS ? SC_DUGKS : (p->scheme == DVBE_BKG ? SC_BKG_FV : SC_CFREE);
+  if (p->recon != DVBE_RECON_LINEAR && p->recon != DVBE_RECON_UPWIND_CELL)
+    return fail(DVBE_ERR_INVALID_ARG, "unknown reconstruction");
+  if (p->path != DVBE_PATH_FUSED && p->path != DVBE_PATH_MULTIPASS)
+    return fail(DVBE_ERR_INVALID_ARG, "unknown step path");
+  pb.recon = p->recon;
+  pb.multipass = p->path == DVBE_PATH_MULTIPASS || p->recon == DVBE_RECON_UPWIND_CELL;
+  if (pb.multipass && (p->precision != DVBE_F64 || p->bkg_fd))
+    return fail(DVBE_ERR_UNSUPPORTED, "the multi-pass step (and the upwind-cell reconstruction) runs "
+                                      "in FP64 and finite-volume form only");
+  if (pb.recon == DVBE_RECON_UPWIND_CELL && p->scheme == DVBE_CFREE_CENTRAL)
+    return fail(DVBE_ERR_UNSUPPORTED, "the central collision-free face has no upwind-cell form");
   if (p->bkg_fd) {
     if (p->scheme != DVBE_BKG || !pb.per_x || !pb.per_y || !uniform(pb.xf) || !uniform(pb.yf))
       return fail(DVBE_ERR_UNSUPPORTED,
@@ -264,6 +281,32 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   else
     pb.b_phi = 2 * dt / (2 * tau + dt); // f_tilde^+ = ((2 tau - dt) f_tilde + 2 dt f_eq) / (2 tau + dt)
   pb.q_face = h / (2 * tau + h);        // f = (2 tau f_bar + h f_eq) / (2 tau + h)
+  pb.b_tp = 2 * dt / (2 * tau + dt);    // f_tilde^+ of every scheme
+  if (pb.multipass) {
+    // cell centres c = -2 .. n+1 (periodic: shifted images; otherwise the
+    // mirror ghost at -1 and n, unused beyond), the central-difference factor
+    // h c / (x_{c+1} - x_{c-1}) of cells -1 .. n, and the offsets of each
+    // face from its two cells' centres, over h c
+    auto tables = [&](const std::vector<double> &f, const std::vector<double> &cb, bool periodic,
+                      std::vector<double> &g, std::vector<double> &off) {
+      const int n = (int)f.size() - 1;
+      const double L = f[n] - f[0];
+      std::vector<double> x(n + 4, 0.0); // x[c+2]
+      for (int c = -1; c <= n; ++c) x[c + 2] = cb[c + 1];
+      x[0] = periodic ? cb[n - 1] - L : 2 * x[1] - x[2];
+      x[n + 3] = periodic ? cb[2] + L : 2 * x[n + 2] - x[n + 1];
+      g.assign(n + 4, 0.0);
+      if (p->scheme != DVBE_CFREE_CENTRAL)
+        for (int c = -1; c <= n; ++c) g[c + 2] = h * c_lat(pb) / (x[c + 3] - x[c + 1]);
+      off.assign(2 * (n + 1), 0.0);
+      for (int k = 0; k <= n; ++k) {
+        off[2 * k] = (f[k] - x[k + 1]) / (h * c_lat(pb));
+        off[2 * k + 1] = (f[k] - x[k + 2]) / (h * c_lat(pb));
+      }
+    };
+    tables(pb.xf, xcb, pb.per_x, pb.xg, pb.xoff);
+    tables(pb.yf, ycb, pb.per_y, pb.yg, pb.yoff);
+  }
   pb.fd_nux = c * dt / (pb.xf[1] - pb.xf[0]);
   pb.fd_nuy = c * dt / (pb.yf[1] - pb.yf[0]);
   // storage layout: rows padded to 128 bytes and at least 64 elements, so a
@@ -328,6 +371,7 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   dp.voly = dp.volx + pb.nx;
 
   memset(&a, 0, sizeof(a));
+  a.wait_limit = kDefaultWaitLimit;
   a.plane = pb.plane;
   a.pitch = pb.pitch;
   a.nx = pb.nx;
@@ -363,9 +407,40 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
 }
 
 void set_strips(CaseArgs &a, int H, int store) {
+  const int cols = strip_cols(store);
   a.H = H;
-  a.strips_x = (a.nx + strip_cols(store) - 1) / strip_cols(store);
+  a.strips_x = (a.nx + cols - 1) / cols;
   a.strips_y = (a.ny + H - 1) / H;
+  // Inner strips: sx >= 1 with (sx + 1) cols <= nx - 1 and sy >= 1 with
+  // (sy + 1) H <= ny - 1, so that the strip's columns i0 - 1 .. i0 + cols
+  // and rows j0 - 1 .. j0 + H are all cells of the mesh.
+  // On a mesh periodic in y every strip row qualifies (rows wrap).
+  const int sxmax = a.nx - 1 - cols >= 0 ? (a.nx - 1 - cols) / cols : 0;
+  const int symax = (a.ny - 1) / H - 1;
+  a.in_x0 = 1;
+  a.in_nx = std::max(0, sxmax);
+  a.in_y0 = a.per_y ? 0 : 1;
+  a.in_ny = a.per_y ? a.strips_y : std::max(0, symax);
+  a.He = H;
+  a.n_edge = 0;
+  if (a.in_nx == 0 || a.in_ny == 0) {
+    a.in_nx = a.in_ny = 0; // one kernel over every strip
+    return;
+  }
+  // the ring in pieces of He rows: the largest divisor of H in 4..8 below H
+  for (int d = 8; d >= 4; --d)
+    if (d < H && H % d == 0) {
+      a.He = d;
+      break;
+    }
+  const long long pieces_y = (a.ny + a.He - 1) / a.He;
+  const long long r0 = (long long)a.in_y0 * (H / a.He);
+  const long long r1 = std::min((long long)(a.in_y0 + a.in_ny) * (H / a.He), pieces_y);
+  a.n_edge = (long long)a.strips_x * pieces_y - (long long)a.in_nx * (r1 - r0);
+}
+
+int kernels_per_step(const CaseArgs &a) {
+  return (long long)a.in_nx * a.in_ny == 0 ? 1 : (a.n_edge > 0 ? 2 : 1);
 }
 
 FieldView view_of(const Problem &pb, void *f) {
@@ -483,6 +558,9 @@ struct dvbe_solver_ {
   CaseArgs args;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  StepStreams ss{}; // main = stream; side stream and fork / join events of the two-kernel step
+  MPArgs mp{};      // multi-pass step: buffers and tables (one allocation), when used
+  char *mpblob = nullptr;
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned *flag = nullptr;
@@ -495,6 +573,45 @@ struct dvbe_solver_ {
   int graph_len = 0;
   CUtensorMap tm[2][2]; // [buffer][main, wrap]
 };
+
+// Buffers and tables of the multi-pass step in one device allocation.
+static dvbe_status alloc_multipass(dvbe_solver s) {
+  const Problem &pb = s->pb;
+  const long long nx = pb.nx, ny = pb.ny;
+  const long long pplane = (nx + 4) * (ny + 4);
+  const long long counts[8] = {9 * pplane, 9 * nx * ny, 9 * (nx + 1) * ny, 9 * nx * (ny + 1),
+                               nx + 4, ny + 4, 2 * (nx + 1), 2 * (ny + 1)};
+  size_t off[8], total = 0;
+  for (int q = 0; q < 8; ++q) {
+    off[q] = total;
+    total += ((size_t)counts[q] * sizeof(double) + 255) / 256 * 256;
+  }
+  s->mpblob = (char *)dmalloc(total, s->stream);
+  if (!s->mpblob) return fail(DVBE_ERR_OOM, "device allocation of the multi-pass buffers failed");
+  const std::vector<double> *tab[4] = {&pb.xg, &pb.yg, &pb.xoff, &pb.yoff};
+  cudaError_t e = cudaMemsetAsync(s->mpblob, 0, total, s->stream);
+  for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(s->mpblob + off[4 + q], tab[q]->data(), sizeof(double) * tab[q]->size(),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "multi-pass set-up");
+  MPArgs &m = s->mp;
+  m.phi = (double *)(s->mpblob + off[0]);
+  m.pplane = pplane;
+  m.tp = (double *)(s->mpblob + off[1]);
+  m.fx = (double *)(s->mpblob + off[2]);
+  m.fy = (double *)(s->mpblob + off[3]);
+  m.xg = (const double *)(s->mpblob + off[4]);
+  m.yg = (const double *)(s->mpblob + off[5]);
+  m.xoff = (const double *)(s->mpblob + off[6]);
+  m.yoff = (const double *)(s->mpblob + off[7]);
+  m.b_tp = pb.b_tp;
+  m.nx = pb.nx;
+  m.ny = pb.ny;
+  m.recon = pb.recon;
+  m.scheme = pb.kernel;
+  return DVBE_OK;
+}
 
 static void drop_graphs(dvbe_solver s) {
   for (int p = 0; p < 2; ++p)
@@ -613,6 +730,10 @@ void dvbe_solver_destroy(dvbe_solver s) {
   dfree(s->red, s->stream);
   dfree(s->uprev, s->stream);
   dfree(s->dp.blob, s->stream);
+  dfree(s->mpblob, s->stream);
+  if (s->ss.side) cudaStreamDestroy(s->ss.side);
+  if (s->ss.fork) cudaEventDestroy(s->ss.fork);
+  if (s->ss.join) cudaEventDestroy(s->ss.join);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -637,6 +758,21 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
     }
     s->own_stream = true;
   }
+  s->ss.main = s->stream;
+  {
+    // DVBE_RING_PRIORITY 1: the ring kernel's stream at the highest priority
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&s->ss.side, cudaStreamNonBlocking,
+                                       DVBE_RING_PRIORITY ? greatest : least);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ss.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ss.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      dvbe_solver_destroy(s);
+      return cuda_fail(e, "side stream of the step");
+    }
+  }
   st = upload_problem(s->pb, s->dp, s->args, s->stream);
   const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
   if (st == DVBE_OK) {
@@ -648,6 +784,7 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
   }
   for (int p = 0; p < 2 && st == DVBE_OK; ++p)
     st = make_tensor_maps(s->pb, s->f[p], &s->tm[p][0], &s->tm[p][1]);
+  if (st == DVBE_OK && s->pb.multipass) st = alloc_multipass(s);
   if (st == DVBE_OK) {
     cudaError_t e = cudaMemsetAsync(s->f[0], 0, fbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, fbytes, s->stream);
@@ -746,16 +883,22 @@ dvbe_status dvbe_get_f(dvbe_solver s, double *ft) {
   return DVBE_OK;
 }
 
+// Kernel launches of one step of this solver.
+static int step_launches(dvbe_solver s) {
+  return s->pb.multipass ? kMultipassKernels : kernels_per_step(s->args);
+}
+
 static cudaError_t launch_one(dvbe_solver s) {
   s->args.tm_main = s->tm[s->cur][0];
   s->args.tm_wrap = s->tm[s->cur][1];
   s->args.fin = s->f[s->cur];
   s->args.fout = s->f[1 - s->cur];
-  cudaError_t e = launch_step(s->pb.store, s->pb.kernel, s->args, s->launch.blocks,
-                              s->launch.warps_per_block, s->stream);
+  cudaError_t e = s->pb.multipass ? launch_multipass(s->args, s->mp, s->stream)
+                                  : launch_step(s->pb.store, s->pb.kernel, s->args, s->launch.blocks,
+                                                s->launch.warps_per_block, s->ss);
   s->cur ^= 1;
   s->steps += 1;
-  s->launches += 1;
+  s->launches += step_launches(s);
   return e;
 }
 
@@ -799,7 +942,7 @@ dvbe_status dvbe_step_async(dvbe_solver s, long long nsteps) {
     while (nsteps >= chunk && e == cudaSuccess) {
       e = cudaGraphLaunch(s->graph[s->cur], s->stream);
       s->steps += chunk;
-      s->launches += chunk;
+      s->launches += (long long)chunk * step_launches(s);
       nsteps -= chunk;
     }
   }
@@ -918,23 +1061,87 @@ dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in) {
   return DVBE_OK;
 }
 
+// Resident blocks per SM of this solver's inner-strip kernel.
+static int inner_blocks_per_sm(const Problem &pb, int wpb) {
+  switch (pb.store) {
+    case ST_F64:
+      return inner_blocks_per_sm_f64(pb.kernel, wpb);
+    case ST_F32:
+    case ST_F32_DEV:
+      return inner_blocks_per_sm_f32(pb.store, pb.kernel, wpb);
+    default:
+      return inner_blocks_per_sm_f16(pb.store, pb.kernel, wpb);
+  }
+}
+
+// Smallest strip height whose inner strips (set_strips) fit in `waves`
+// waves of `slots` resident warps; 0 if the mesh has no inner strips.
+static int wave_fitted_rows(const CaseArgs &args, int store, long long slots, int waves) {
+  if (slots <= 0) return 0;
+  CaseArgs t = args;
+  for (int H = 4; H <= t.ny; ++H) {
+    set_strips(t, H, store);
+    const long long items = (long long)t.in_nx * t.in_ny;
+    if (items == 0) return 0;
+    if (items <= (long long)waves * slots) return H;
+  }
+  return 0;
+}
+
+static std::string solver_tune_key(dvbe_solver s) {
+  char b[160];
+  snprintf(b, sizeof b, "k_step|kernel %d|store %d|%dx%d|periodic %d%d", s->pb.kernel, s->pb.store,
+           s->pb.nx, s->pb.ny, (int)s->pb.per_x, (int)s->pb.per_y);
+  return tune_key(b);
+}
+
+static void apply_launch(dvbe_solver s, const dvbe_launch &l) {
+  s->launch = l;
+  set_strips(s->args, l.strip_rows, s->pb.store);
+  drop_graphs(s);
+}
+
 dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
   if (!s || steps < 1) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  const dvbe_launch saved = s->launch;
+  const std::string key = solver_tune_key(s);
+  TuneEntry hit;
+  if (tune_lookup(key, &hit) && hit.strip_rows >= 1 && hit.warps_per_block >= 1 &&
+      hit.warps_per_block <= 8 && hit.blocks >= 0) {
+    dvbe_status st = dvbe_sync(s);
+    if (st != DVBE_OK && st != DVBE_ERR_DIVERGED) return st;
+    apply_launch(s, {hit.strip_rows, hit.warps_per_block, hit.blocks, saved.graph_chunk});
+    if (best_ms) *best_ms = hit.ms;
+    return DVBE_OK;
+  }
   const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
   void *backup = dmalloc(fbytes, s->stream);
   if (!backup) return fail(DVBE_ERR_OOM, "device allocation failed");
   cudaError_t e = cudaMemcpyAsync(backup, s->f[s->cur], fbytes, cudaMemcpyDeviceToDevice, s->stream);
   const int saved_cur = s->cur;
   const long long saved_steps = s->steps;
-  const dvbe_launch saved = s->launch;
   std::vector<dvbe_launch> cand;
-  const int rows[] = {16, 32, 64, 128, 256};
+  auto add = [&](int H, int w, int blocks) {
+    for (auto &c : cand)
+      if (c.strip_rows == H && c.warps_per_block == w && c.blocks == blocks) return;
+    cand.push_back({H, w, blocks, 0});
+  };
+  const int rows[] = {8, 16, 24, 32, 48, 64, 128, 256};
   const int wpbs[] = {2, 4, 8};
-  for (int H : rows)
-    for (int w : wpbs) {
-      cand.push_back({H, w, 0, 0});
-      cand.push_back({H, w, sm_count() * (32 / w), 0});
+  for (int w : wpbs) {
+    const int wave = inner_blocks_per_sm(s->pb, w) * sm_count(); // blocks in one wave
+    std::vector<int> hs;
+    for (int H : rows)
+      if (H <= 16 || H <= 2 * s->pb.ny) hs.push_back(H);
+    for (int k = 1; k <= 3; ++k) {
+      const int H = wave_fitted_rows(s->args, s->pb.store, (long long)wave * w, k);
+      if (H > 0) hs.push_back(H);
     }
+    for (int H : hs) {
+      add(H, w, 0);
+      if (wave > 0) add(H, w, wave);
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -942,10 +1149,7 @@ dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
   dvbe_launch bestc = saved;
   for (auto &c : cand) {
     if (e != cudaSuccess) break;
-    if (c.strip_rows > 2 * s->pb.ny && c.strip_rows > 16) continue;
-    s->launch = c;
-    s->launch.graph_chunk = 0;
-    set_strips(s->args, c.strip_rows, s->pb.store);
+    apply_launch(s, c);
     e = launch_one(s); // warm-up
     if (e != cudaSuccess) break;
     cudaEventRecord(e0, s->stream);
@@ -970,10 +1174,14 @@ dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   dfree(backup, s->stream);
   bestc.graph_chunk = saved.graph_chunk;
-  s->launch = bestc;
-  set_strips(s->args, bestc.strip_rows, s->pb.store);
-  drop_graphs(s);
+  apply_launch(s, bestc);
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  TuneEntry te;
+  te.strip_rows = bestc.strip_rows;
+  te.warps_per_block = bestc.warps_per_block;
+  te.blocks = bestc.blocks;
+  te.ms = best;
+  tune_store(key, te);
   if (best_ms) *best_ms = best;
   return DVBE_OK;
 }
@@ -991,6 +1199,83 @@ dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch, long 
 dvbe_status dvbe_launch_count(dvbe_solver s, long long *count) {
   if (!s || !count) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
   *count = s->launches;
+  return DVBE_OK;
+}
+
+static dvbe_status copy_line(dvbe_solver s, int axis, int index, int lo, int hi, void *buf,
+                             int to_buf, const char *what) {
+  if (!s || !buf) return fail(DVBE_ERR_INVALID_ARG, std::string(what) + ": NULL argument");
+  const int nidx = axis == 0 ? s->pb.nx : s->pb.ny, nlen = axis == 0 ? s->pb.ny : s->pb.nx;
+  if ((axis != 0 && axis != 1) || index < 0 || index >= nidx || lo < 0 || hi > nlen || lo >= hi)
+    return fail(DVBE_ERR_INVALID_ARG, std::string(what) + ": line outside the mesh");
+  cudaError_t e = aux_copy_line(cur_view(s), s->pb.elem, axis, index, lo, hi - lo, buf, to_buf, s->stream);
+  s->launches += 1;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_pack_line(dvbe_solver s, int axis, int index, int lo, int hi, void *dev_buf) {
+  return copy_line(s, axis, index, lo, hi, dev_buf, 1, "pack_line");
+}
+
+dvbe_status dvbe_unpack_line(dvbe_solver s, int axis, int index, int lo, int hi, const void *dev_buf) {
+  return copy_line(s, axis, index, lo, hi, const_cast<void *>(dev_buf), 0, "unpack_line");
+}
+
+dvbe_status dvbe_conserved_window(dvbe_solver s, int i0, int j0, int nx, int ny, double out[3]) {
+  if (!s || !out) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  if (i0 < 0 || j0 < 0 || nx < 1 || ny < 1 || i0 + nx > s->pb.nx || j0 + ny > s->pb.ny)
+    return fail(DVBE_ERR_INVALID_ARG, "window outside the mesh");
+  FieldView v = cur_view(s);
+  v.f = (char *)v.f + ((long long)j0 * v.pitch + i0) * s->pb.elem;
+  v.nx = nx;
+  v.ny = ny;
+  double *res = s->red + kReduceBlocks * 3;
+  cudaError_t e = aux_conserved(v, s->dp.volx + i0, s->dp.voly + j0, s->red, res, s->stream);
+  s->launches += 2;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "conserved_window");
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_state_bytes(dvbe_solver s, size_t *bytes) {
+  if (!s || !bytes) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  *bytes = (size_t)s->pb.plane * 9 * s->pb.elem;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_save_state(dvbe_solver s, void *host, size_t bytes, long long *step) {
+  if (!s || !host) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
+  const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
+  if (bytes != fbytes)
+    return fail(DVBE_ERR_INVALID_ARG, "state buffer must hold " + std::to_string(fbytes) + " bytes");
+  cudaError_t e = cudaMemcpyAsync(host, s->f[s->cur], fbytes, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "save_state");
+  if (step) *step = s->steps;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_load_state(dvbe_solver s, const void *host, size_t bytes, long long step) {
+  if (!s || !host || step < 0) return fail(DVBE_ERR_INVALID_ARG, "NULL argument or negative step");
+  const size_t fbytes = (size_t)s->pb.plane * 9 * s->pb.elem;
+  if (bytes != fbytes)
+    return fail(DVBE_ERR_INVALID_ARG, "state buffer must hold " + std::to_string(fbytes) + " bytes");
+  cudaError_t e = cudaMemcpyAsync(s->f[s->cur], host, fbytes, cudaMemcpyHostToDevice, s->stream);
+  dvbe_status st = after_init(s, e, "load_state");
+  if (st != DVBE_OK) return st;
+  s->steps = step;
+  return DVBE_OK;
+}
+
+dvbe_status dvbe_set_wait_limit(dvbe_solver s, long long polls) {
+  if (!s || polls < 0) return fail(DVBE_ERR_INVALID_ARG, "NULL solver or negative poll count");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_wait_limit");
+  s->args.wait_limit = (unsigned long long)polls;
+  drop_graphs(s); // captured launches hold the old arguments
   return DVBE_OK;
 }
 

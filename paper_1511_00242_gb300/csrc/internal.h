@@ -58,6 +58,21 @@ struct CaseArgs {
   int nx, ny;
   int per_x, per_y;
   int strips_x, strips_y, H; // strip decomposition: strip_cols columns x H rows per warp
+  // Partition of the strips for the two-kernel step: the inner rectangle of
+  // strips [in_x0, in_x0 + in_nx) x [in_y0, in_y0 + in_ny) (H rows each, the
+  // last possibly fewer) touches no boundary, wrapped column or ghost row
+  // (rows wrap by the copy coordinate when the mesh is periodic in y) and
+  // runs in a kernel compiled without boundary code; the ring of strips
+  // around it runs in a second kernel, cut into pieces of He rows (He divides
+  // H) for finer work items.  in_nx * in_ny == 0: one kernel covers every
+  // strip.
+  int in_x0, in_nx, in_y0, in_ny;
+  int He;
+  long long n_edge; // work items of the ring
+  // Polls of a row copy that has not landed, after its first test, before
+  // the warp gives up (flag bit 1, DVBE_ERR_TIMEOUT on the host); 0: every
+  // wait gives up at once.
+  unsigned long long wait_limit;
 
   double rho0;
   double b_phi;          // phi = delta + b (delta_eq - delta): DUGKS f_bar^+, BKG f_tilde^+,
@@ -76,12 +91,23 @@ struct CaseArgs {
   int nseg[4];
   SegParam seg[4][DVBE_MAX_SEGMENTS];
 
-  unsigned int *flag; // bit 0: divergence seen
+  unsigned int *flag; // bit 0: divergence seen; bit 1: a bounded wait ran out
+};
+
+// Default of CaseArgs::wait_limit.
+constexpr unsigned long long kDefaultWaitLimit = 1ull << 24;
+
+// Streams of a step: the main stream, and a side stream with two events to
+// run the ring kernel beside the inner kernel (fork: main -> side, join:
+// side -> main).
+struct StepStreams {
+  cudaStream_t main, side;
+  cudaEvent_t fork, join;
 };
 
 // Step launchers (one translation unit per storage mode).
 cudaError_t launch_step(int store, int scheme, const CaseArgs &a, int blocks, int warps_per_block,
-                        cudaStream_t s);
+                        const StepStreams &ss);
 cudaError_t launch_step_batch(int store, int scheme, const CaseArgs *d_cases,
                               const long long *d_prefix, int ncases, long long nitems,
                               unsigned long long *d_queue, int blocks, int warps_per_block,
@@ -117,6 +143,11 @@ cudaError_t aux_moments(const FieldView &v, double *d_rho, double *d_ux, double 
 constexpr int kReduceBlocks = 296;
 cudaError_t aux_conserved(const FieldView &v, const double *d_vol_x, const double *d_vol_y,
                           double *d_partials, double *d_out, cudaStream_t s);
+// One line of cells (axis 0: a column over rows lo..lo+n-1, axis 1: a row
+// over columns lo..lo+n-1) of all nine fields to / from a dense buffer
+// [9][n] of elem-byte elements, as stored.
+cudaError_t aux_copy_line(const FieldView &v, int elem, int axis, int index, int lo, int n,
+                          void *buf, int to_buf, cudaStream_t s);
 // sums |u - ref|^2 and |ref|^2 (mode 0: ref = given arrays, E_u); mode 1:
 // residual against d_ua/d_va = previous velocity, which is then overwritten.
 cudaError_t aux_velocity_error(const FieldView &v, double *d_ua, double *d_va, int mode,

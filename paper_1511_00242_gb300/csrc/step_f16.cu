@@ -3,7 +3,7 @@
 
 namespace dvbe {
 cudaError_t launch_step_f16(int store, int scheme, const CaseArgs &a, int blocks, int wpb,
-                            cudaStream_t s) {
+                            const StepStreams &s) {
   if (store == ST_F16_DEV) return launch_step_impl<ST_F16_DEV>(scheme, a, blocks, wpb, s);
   return launch_step_impl<ST_BF16_DEV>(scheme, a, blocks, wpb, s);
 }
@@ -12,5 +12,9 @@ cudaError_t launch_batch_f16(int store, int scheme, const CaseArgs *c, const lon
                              cudaStream_t s) {
   if (store == ST_F16_DEV) return launch_batch_impl<ST_F16_DEV>(scheme, c, p, n, ni, q, blocks, wpb, s);
   return launch_batch_impl<ST_BF16_DEV>(scheme, c, p, n, ni, q, blocks, wpb, s);
+}
+int inner_blocks_per_sm_f16(int store, int scheme, int wpb) {
+  if (store == ST_F16_DEV) return inner_blocks_per_sm_impl<ST_F16_DEV>(scheme, wpb);
+  return inner_blocks_per_sm_impl<ST_BF16_DEV>(scheme, wpb);
 }
 } // namespace dvbe

@@ -63,6 +63,15 @@
 #ifndef DVBE_PAIR_BKG_UNROLL
 #define DVBE_PAIR_BKG_UNROLL 0
 #endif
+// The ring kernel of the two-kernel step: 1 = on the side stream beside the
+// inner kernel, 0 = after it on the main stream; DVBE_RING_FIRST 1 launches
+// it before the inner kernel.
+#ifndef DVBE_RING_CONCURRENT
+#define DVBE_RING_CONCURRENT 1
+#endif
+#ifndef DVBE_RING_FIRST
+#define DVBE_RING_FIRST 0
+#endif
 // Shared-memory stages of each warp's row pipeline (rows j and j+1 are held,
 // the others are in flight).
 #ifndef DVBE_STAGES
@@ -73,6 +82,9 @@ namespace dvbe {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Row paths compiled into a kernel (Strip::run).
+enum { PATH_BOTH = 0, PATH_INNER = 1, PATH_EDGE = 2 };
 
 // D2Q9 lattice directions (xi = c e, Sec 2.1) and weights.
 __host__ __device__ constexpr int EX(int a) {
@@ -482,6 +494,17 @@ __device__ __forceinline__ void fence_proxy_async_pred(uint32_t on) {
                : "memory");
 }
 
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Test that may suspend the thread for a hardware-defined time.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -585,9 +608,12 @@ __device__ __forceinline__ void st_lane(__nv_bfloat16 *p, F2 v, bool on) {
                : "memory");
 }
 
-// Waits longer than this many polls are treated as a failure: the warp sets
-// bit 1 of the case flag and abandons its work (the host reports a timeout).
-constexpr uint32_t kSpinLimit = 1u << 24;
+// A row copy still pending after CaseArgs::wait_limit polls, or after
+// kWaitCycles SM clock cycles (about a second), is a failure: the warp stops
+// fetching, waits (with the same bounds) for the copies it has in flight,
+// sets bit 1 of the case flag and leaves; the host reports DVBE_ERR_TIMEOUT.
+constexpr uint32_t kDrainPolls = 1u << 22;
+constexpr long long kWaitCycles = 1ll << 31;
 
 // Shared-memory geometry of one warp's row pipeline for element size ES and
 // NC columns per lane.
@@ -634,10 +660,13 @@ template <int SCHEME, int ST> struct Strip {
   uint32_t offc[NC]; // byte offset of each column inside a stage (boundary strips)
   uint32_t lds_off;  // byte offset of the first column (inner strips: one aligned load)
   bool per_x, per_y, touchW, touchE, wrapW, wrapE, out_lane;
-  V b_phi, q_face;
+  V b_phi;       // phi = d + b_phi (d_eq - d)
+  V q_face;      // DUGKS face: f = f_bar + q (f_eq - f_bar)
   // x-face coefficients of this lane's columns: right part of the west face,
-  // left part of the east face; tangential / update factors of the column.
-  V cR[3], cL[3], tR0, tL0, txc, ntxc, cxu, ncxu;
+  // left part of the east face; tangential / update factors of the column
+  // (directions of either sign use them with the operands of the difference
+  // they multiply swapped, so no negated copies are held).
+  V cR[3], cL[3], tR0, tL0, txc, cxu;
   // BKG-FD stencil factors
   Real kx1, kx2, ky1, ky2, kxy;
   int segS[NC], segN[NC];
@@ -654,9 +683,12 @@ template <int SCHEME, int ST> struct Strip {
   uint32_t cpar;
   int nfetch, nissued, nwaited; // of the current strip
   int Fa;                       // logical row of fetch 0
+  // Warp-uniform: a wait ran out.  From then on nothing is issued and
+  // nothing advances (cslot / cpar stay at the fetch that ran out, nwaited
+  // counts the fetches completed before it), so the copies still in flight
+  // are fetches nwaited .. nissued-1 on stages cslot, cslot + 1, ...
   bool timeout;
-  int tslot;     // stage of the wait that ran out
-  uint32_t tpar; // and its parity
+  unsigned long long wlim; // polls before a pending copy counts as lost
 
   __device__ __forceinline__ Strip(const CaseArgs &args, int lane_, uint32_t sbase_)
       : A(args), lane(lane_), sbase(sbase_) {
@@ -666,8 +698,7 @@ template <int SCHEME, int ST> struct Strip {
     cpar = 0;
     bad = false;
     timeout = false;
-    tslot = 0;
-    tpar = 0;
+    wlim = args.wait_limit;
   }
 
   __device__ __forceinline__ void init_barriers() {
@@ -729,9 +760,7 @@ template <int SCHEME, int ST> struct Strip {
       set_comp(tR0, c, thW);
       set_comp(tL0, c, Real(1) - thE);
       set_comp(txc, c, xct[ic + 1]);
-      set_comp(ntxc, c, -xct[ic + 1]);
       set_comp(cxu, c, xcu[ic + 1]);
-      set_comp(ncxu, c, -xcu[ic + 1]);
       const int icc = min(max(i, 0), nx - 1);
       segS[c] = per_y ? 0 : A.segid[2][icc];
       segN[c] = per_y ? 0 : A.segid[3][icc];
@@ -771,11 +800,12 @@ template <int SCHEME, int ST> struct Strip {
 
   // ---- row pipeline: fetch number q of this strip is logical row Fa + q
   template <bool INT> __device__ __forceinline__ void issue() {
+    if (timeout) return;
     const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
-    const int r = INT ? Fa + nissued : wrapr(Fa + nissued);
-    tma_row_pred((uint32_t)(lane == 0 && !timeout), bar, txbytes, dst, &A.tm_main, xs, r);
+    const int r = wrapr(Fa + nissued); // periodic in y: rows -1 and ny wrap
+    tma_row_pred((uint32_t)(lane == 0), bar, txbytes, dst, &A.tm_main, xs, r);
     if (!INT && (wrapW || wrapE)) {
-      if (lane == 0 && !timeout) {
+      if (lane == 0) {
         if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, xwrapW, r, 0, bar);
         if (wrapE) tma_load3(dst + P::MAINB + P::WRAPB, &A.tm_wrap, 0, r, 0, bar);
       }
@@ -784,21 +814,27 @@ template <int SCHEME, int ST> struct Strip {
     ++nissued;
   }
 
-  // Bounded wait after a failed first poll; a lane whose wait runs out stops
-  // waiting from then on (the warp checks the flag once per strip).
+  // Bounded wait after a failed first test: every lane polls until all see
+  // the phase complete, at most wlim times and kWaitCycles cycles; then the
+  // wait has run out.
   __device__ __forceinline__ void wait_slow(uint32_t bar, uint32_t par) {
-    if (timeout) return;
-    for (uint32_t n = 0; n < kSpinLimit; ++n)
-      if (mbar_try_wait(bar, par)) return;
+    const long long t0 = clock64();
+    for (unsigned long long n = 0; n < wlim; ++n) {
+      if (__all_sync(kFull, mbar_try_wait(bar, par))) return;
+      if (__any_sync(kFull, clock64() - t0 > kWaitCycles)) break;
+    }
     timeout = true;
-    tslot = cslot;
-    tpar = par;
   }
 
-  // Wait for the next fetch in order; returns its stage address.
+  // Wait for the next fetch in order; returns its stage address (after a
+  // timeout: the stage of the lost fetch, whose contents are not used).
   __device__ __forceinline__ uint32_t wait() {
     const uint32_t st = sbase + cslot * P::STAGEB, bar = bbase + 8 * cslot;
-    if (!mbar_try_wait(bar, cpar)) wait_slow(bar, cpar);
+    if (timeout) return st;
+    if (wlim == 0 || !__all_sync(kFull, mbar_test_wait(bar, cpar))) {
+      wait_slow(bar, cpar); // a budget of zero polls runs out at once
+      if (timeout) return st;
+    }
     ++nwaited;
     if (++cslot == P::NS) {
       cslot = 0;
@@ -981,7 +1017,10 @@ template <int SCHEME, int ST> struct Strip {
         own = vfma(ap, Pl[a], bm * Pu[a]);
       else
         own = vfma(am, Pl[a], bp * Pu[a]);
-      if (EX(a) != 0) own = vfma(EX(a) > 0 ? ntxc : txc, shift_r(B) - shift_l(B), own);
+      if (EX(a) != 0) {
+        const V Br = shift_r(B), Bl = shift_l(B);
+        own = vfma(txc, EX(a) > 0 ? Bl - Br : Br - Bl, own);
+      }
       F[a] = own;
     }
     if (!INT && !per_y && (kf == 0 || kf == ny)) {
@@ -1120,16 +1159,19 @@ template <int SCHEME, int ST> struct Strip {
         xface<INT>(j, tyc, Pa, Pb, Pc, F);
 #pragma unroll
         for (int a = 0; a < 9; ++a)
-          if (EX(a) != 0) v[a] = vfma(EX(a) > 0 ? ncxu : cxu, shift_r(F[a]) - F[a], v[a]);
+          if (EX(a) != 0) {
+            const V Fr = shift_r(F[a]);
+            v[a] = vfma(cxu, EX(a) > 0 ? F[a] - Fr : Fr - F[a], v[a]);
+          }
       }
       {
         V F[9];
         yface<INT>(j + 1, th, sl, Pb, Pc, F);
-        const V cy = V(cyu), ncy = V(-cyu);
+        const V cy = V(cyu);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
           if (EY(a) != 0) {
-            v[a] = vfma(EY(a) > 0 ? ncy : cy, F[a] - FS[a], v[a]);
+            v[a] = vfma(cy, EY(a) > 0 ? FS[a] - F[a] : F[a] - FS[a], v[a]);
             FS[a] = F[a];
           }
         }
@@ -1200,31 +1242,41 @@ template <int SCHEME, int ST> struct Strip {
     }
   }
 
-  __device__ __forceinline__ void run(int sx, int sy) {
+  // Column strip sx, rows [j0, jend).  PATHS: PATH_BOTH compiles both row
+  // paths and picks the inner one for strips that touch no boundary;
+  // PATH_INNER only the inner path (every strip given is inner); PATH_EDGE
+  // only the general path, which is correct for any strip.
+  template <int PATHS> __device__ __forceinline__ void run(int sx, int j0, int jend) {
     setup(sx);
-    const int j0 = sy * A.H;
-    const int jend = min(j0 + A.H, ny);
-    // inner strip: its columns i0 - 1 .. i0 + COLS and the rows j0-1 .. jend all exist
-    const bool inner = i0 >= 1 && i0 + COLS <= nx - 1 && j0 >= 1 && jend <= ny - 1;
-    if (inner)
+    if constexpr (PATHS == PATH_INNER) {
       run_t<true>(j0, jend);
-    else
+    } else if constexpr (PATHS == PATH_EDGE) {
       run_t<false>(j0, jend);
+    } else {
+      // inner strip: its columns i0 - 1 .. i0 + COLS are cells, and so are the
+      // rows j0-1 .. jend, or the mesh is periodic in y (rows wrap)
+      const bool inner = i0 >= 1 && i0 + COLS <= nx - 1 && (per_y || (j0 >= 1 && jend <= ny - 1));
+      if (inner)
+        run_t<true>(j0, jend);
+      else
+        run_t<false>(j0, jend);
+    }
   }
 
-  // After a timed-out wait: give the copies still in flight a bounded time
-  // to land before the warp leaves (their shared memory must stay valid).
-  // The fetch that timed out was on stage tslot with parity tpar; it and the
-  // later issued ones are outstanding.
+  // After a wait ran out: give every copy still in flight a bounded time to
+  // land before the warp leaves (its shared memory must stay valid until
+  // then).  Fetches nwaited .. nissued-1 are outstanding, in ring order from
+  // stage cslot with parity cpar (neither advanced after the timeout).
   __device__ __forceinline__ void drain() {
     if (!timeout) return;
-    int s = tslot;
-    uint32_t par = tpar;
-    const int waited_ok = nwaited - 1; // the timed-out wait was counted
-    for (int q = waited_ok; q < nissued; ++q) {
-      uint32_t n = 0;
-      while (!mbar_try_wait(bbase + 8 * s, par) && ++n < (1u << 16)) {
-      }
+    int s = cslot;
+    uint32_t par = cpar;
+    for (int q = nwaited; q < nissued; ++q) {
+      const long long t0 = clock64();
+      for (uint32_t n = 0; n < kDrainPolls; ++n)
+        if (__all_sync(kFull, mbar_try_wait(bbase + 8 * s, par)) ||
+            __any_sync(kFull, clock64() - t0 > kWaitCycles))
+          break;
       if (++s == P::NS) {
         s = 0;
         par ^= 1u;
@@ -1234,33 +1286,119 @@ template <int SCHEME, int ST> struct Strip {
 };
 
 // Blocks of 256 threads per SM the step kernel is compiled for.
-template <int SCHEME, int ST> constexpr int min_blocks() {
+template <int SCHEME, int ST> __host__ __device__ constexpr int min_blocks() {
   return LaneT<typename StoreT<ST>::Real>::NC == 2
              ? DVBE_PAIR_MINB
              : (SCHEME == SC_DUGKS ? DVBE_DUGKS_MINB : DVBE_BKG_MINB);
 }
 
-template <int SCHEME, int ST>
-__global__ void __launch_bounds__(256, min_blocks<SCHEME, ST>())
-    k_step(const __grid_constant__ CaseArgs A) {
+// Work items of one step.  PART_ALL: every strip of H rows (one kernel).
+// PART_INNER: the inner rectangle of strips (CaseArgs::in_*), H rows each.
+// PART_EDGE: the ring of strips around it, in pieces of He rows: a band of
+// whole-width rows below the rectangle, the strips left and right of it, and
+// a band above it.
+enum { PART_ALL = 0, PART_INNER = 1, PART_EDGE = 2 };
+
+template <int PART> __device__ __forceinline__ long long part_items(const CaseArgs &A) {
+  if constexpr (PART == PART_INNER)
+    return (long long)A.in_nx * A.in_ny;
+  else if constexpr (PART == PART_EDGE)
+    return A.n_edge;
+  else
+    return (long long)A.strips_x * A.strips_y;
+}
+
+template <int PART>
+__device__ __forceinline__ void part_item(const CaseArgs &A, long long it, int &sx, int &j0,
+                                          int &jend) {
+  if constexpr (PART == PART_INNER) {
+    sx = A.in_x0 + (int)(it % A.in_nx);
+    j0 = (A.in_y0 + (int)(it / A.in_nx)) * A.H;
+    jend = min(j0 + A.H, A.ny);
+  } else if constexpr (PART == PART_EDGE) {
+    const int k = A.H / A.He; // pieces per strip height
+    const long long pieces_y = (A.ny + A.He - 1) / A.He;
+    const long long r0 = (long long)A.in_y0 * k;
+    const long long r1 = min((long long)(A.in_y0 + A.in_ny) * k, pieces_y);
+    const long long nex = A.strips_x - A.in_nx; // ring strips beside the rectangle
+    long long q, e = it;
+    if (e < r0 * A.strips_x) {
+      q = e / A.strips_x;
+      sx = (int)(e % A.strips_x);
+    } else if ((e -= r0 * A.strips_x) < (r1 - r0) * nex) {
+      q = r0 + e / nex;
+      const int m = (int)(e % nex);
+      sx = m < A.in_x0 ? m : m + A.in_nx;
+    } else {
+      e -= (r1 - r0) * nex;
+      q = r1 + e / A.strips_x;
+      sx = (int)(e % A.strips_x);
+    }
+    j0 = (int)q * A.He;
+    jend = min(j0 + A.He, A.ny);
+  } else {
+    sx = (int)(it % A.strips_x);
+    j0 = (int)(it / A.strips_x) * A.H;
+    jend = min(j0 + A.H, A.ny);
+  }
+}
+
+template <int PART> __host__ __device__ constexpr int part_paths() {
+  return PART == PART_INNER ? PATH_INNER : (PART == PART_EDGE ? PATH_EDGE : PATH_BOTH);
+}
+
+// The strips of one part, each warp taking items gw, gw + nw, ...
+template <int SCHEME, int ST, int PART> __device__ __forceinline__ void step_part(const CaseArgs &A) {
   extern __shared__ __align__(128) unsigned char smem[];
   using P = typename Strip<SCHEME, ST>::P;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nitems = (long long)A.strips_x * A.strips_y;
+  const long long nitems = part_items<PART>(A);
   Strip<SCHEME, ST> s(A, lane, smem_u32(smem) + wib * P::WARPB);
   s.init_barriers();
   for (long long it = gw; it < nitems; it += nw) {
-    s.run((int)(it % A.strips_x), (int)(it / A.strips_x));
-    if (__any_sync(kFull, s.timeout)) break;
+    int sx, j0, jend;
+    part_item<PART>(A, it, sx, j0, jend);
+    s.template run<part_paths<PART>()>(sx, j0, jend);
+    if (s.timeout) break; // warp-uniform
   }
-  if (__any_sync(kFull, s.timeout)) {
+  if (s.timeout) {
     s.drain();
     if (lane == 0) atomicOr(A.flag, 2u);
   }
   if (__any_sync(kFull, s.bad) && lane == 0) atomicOr(A.flag, 1u);
+}
+
+template <int SCHEME, int ST, int PART>
+__global__ void __launch_bounds__(256, min_blocks<SCHEME, ST>())
+    k_step(const __grid_constant__ CaseArgs A) {
+  step_part<SCHEME, ST, PART>(A);
+}
+
+// The inner strips alone: without boundary code the kernel needs fewer
+// registers than the general path, so more warps fit on an SM.  Register cap
+// per thread: DVBE_PAIR_INNER_MAXREG for paired FP32 strips (168: 12 warps
+// per SM), and for FP64 the occupancy target of min_blocks.
+#ifndef DVBE_PAIR_INNER_MAXREG
+#define DVBE_PAIR_INNER_MAXREG 168
+#endif
+template <int SCHEME, int ST> __host__ __device__ constexpr int inner_maxreg() {
+  return LaneT<typename StoreT<ST>::Real>::NC == 2
+             ? DVBE_PAIR_INNER_MAXREG
+             : (65536 / (256 * min_blocks<SCHEME, ST>()) > 255 ? 255
+                                                               : 65536 / (256 * min_blocks<SCHEME, ST>()));
+}
+template <int SCHEME, int ST>
+__global__ void __maxnreg__((inner_maxreg<SCHEME, ST>())) k_step_inner(const __grid_constant__ CaseArgs A) {
+  step_part<SCHEME, ST, PART_INNER>(A);
+}
+// The ring of boundary strips: the general path alone also fits the cap
+// with little spilling, so it too runs at the inner kernel's occupancy.
+template <int SCHEME, int ST>
+__global__ void __maxnreg__((inner_maxreg<SCHEME, ST>())) k_step_edge(const __grid_constant__ CaseArgs A) {
+  step_part<SCHEME, ST, PART_EDGE>(A);
 }
 
 // Batched form: warps take strips of all cases from one queue.
@@ -1275,7 +1413,6 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t sb = smem_u32(smem) + wib * P::WARPB;
   int pipe_slot = 0;       // stage of this warp's next fetch
   uint32_t pipe_phase = 0; // parity to wait for on each stage
-  bool timeout = false;
   {
     Strip<SCHEME, ST> s0(cases[0], lane, sb);
     s0.init_barriers();
@@ -1304,18 +1441,18 @@ __global__ void __launch_bounds__(256, 1)
     s.islot = pipe_slot;
     s.cslot = pipe_slot;
     s.cpar = pipe_phase;
-    s.run((int)(local % A.strips_x), (int)(local / A.strips_x));
+    int sx, j0, jend;
+    part_item<PART_ALL>(A, local, sx, j0, jend);
+    s.template run<PATH_BOTH>(sx, j0, jend);
     pipe_slot = s.cslot;
     pipe_phase = s.cpar;
     if (__any_sync(kFull, s.bad) && lane == 0) atomicOr(A.flag, 1u);
-    if (__any_sync(kFull, s.timeout)) {
+    if (s.timeout) { // warp-uniform
       s.drain();
       if (lane == 0) atomicOr(A.flag, 2u);
-      timeout = true;
       break;
     }
   }
-  (void)timeout;
 }
 
 } // namespace dev
@@ -1329,20 +1466,96 @@ template <typename K> cudaError_t allow_smem(K kern, int bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int ST>
-cudaError_t launch_step_impl(int scheme, const CaseArgs &a, int blocks, int wpb, cudaStream_t s) {
+// One step.  Meshes with inner strips: the inner kernel on the main stream
+// and the ring kernel on the side stream, forked from and joined back into
+// the main stream, so the two run concurrently (the ring's short pieces fill
+// the inner kernel's last wave); both read f_in and write disjoint cells of
+// f_out.  Otherwise one kernel over every strip.
+template <int SCHEME, int ST>
+cudaError_t launch_step_scheme(const CaseArgs &a, int blocks, int wpb, const StepStreams &ss) {
   dim3 block(32 * wpb);
   const int smem = wpb * warp_smem<ST>();
-  const long long nitems = (long long)a.strips_x * a.strips_y;
-  if (blocks <= 0) blocks = (int)((nitems + wpb - 1) / wpb);
-  auto kern = scheme == SC_DUGKS    ? dev::k_step<SC_DUGKS, ST>
-              : scheme == SC_BKG_FV ? dev::k_step<SC_BKG_FV, ST>
-              : scheme == SC_BKG_FD ? dev::k_step<SC_BKG_FD, ST>
-                                    : dev::k_step<SC_CFREE, ST>;
-  cudaError_t e = allow_smem(kern, smem);
+  const long long n_inner = (long long)a.in_nx * a.in_ny;
+  cudaError_t e = cudaSuccess;
+  if (n_inner == 0) {
+    auto kern = dev::k_step<SCHEME, ST, dev::PART_ALL>;
+    const long long nitems = (long long)a.strips_x * a.strips_y;
+    if (blocks <= 0) blocks = (int)((nitems + wpb - 1) / wpb);
+    e = allow_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, block, smem, ss.main>>>(a);
+    return cudaGetLastError();
+  }
+  auto ki = dev::k_step_inner<SCHEME, ST>;
+  auto ke = dev::k_step_edge<SCHEME, ST>;
+  e = allow_smem(ki, smem);
+  if (e == cudaSuccess) e = allow_smem(ke, smem);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, block, smem, s>>>(a);
-  return cudaGetLastError();
+  const bool ring = a.n_edge > 0;
+  const bool fork = ring && DVBE_RING_CONCURRENT;
+  const cudaStream_t rs = fork ? ss.side : ss.main;
+  const int ring_blocks = (int)((a.n_edge + wpb - 1) / wpb);
+  if (fork) {
+    e = cudaEventRecord(ss.fork, ss.main);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
+    if (e != cudaSuccess) return e;
+  }
+  if (ring && DVBE_RING_FIRST) {
+    ke<<<ring_blocks, block, smem, rs>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (blocks <= 0) blocks = (int)((n_inner + wpb - 1) / wpb);
+  ki<<<blocks, block, smem, ss.main>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !ring) return e;
+  if (!DVBE_RING_FIRST) {
+    ke<<<ring_blocks, block, smem, rs>>>(a);
+    e = cudaGetLastError();
+  }
+  if (fork && e == cudaSuccess) e = cudaEventRecord(ss.join, ss.side);
+  if (fork && e == cudaSuccess) e = cudaStreamWaitEvent(ss.main, ss.join, 0);
+  return e;
+}
+
+template <int ST>
+cudaError_t launch_step_impl(int scheme, const CaseArgs &a, int blocks, int wpb, const StepStreams &ss) {
+  switch (scheme) {
+    case SC_DUGKS:
+      return launch_step_scheme<SC_DUGKS, ST>(a, blocks, wpb, ss);
+    case SC_BKG_FV:
+      return launch_step_scheme<SC_BKG_FV, ST>(a, blocks, wpb, ss);
+    case SC_BKG_FD:
+      return launch_step_scheme<SC_BKG_FD, ST>(a, blocks, wpb, ss);
+    default:
+      return launch_step_scheme<SC_CFREE, ST>(a, blocks, wpb, ss);
+  }
+}
+
+// Resident blocks per SM of the inner-strip kernel (0 if the query fails).
+template <int SCHEME, int ST> int inner_blocks_per_sm_scheme(int wpb) {
+  auto kern = dev::k_step_inner<SCHEME, ST>;
+  const int smem = wpb * warp_smem<ST>();
+  int n = 0;
+  if (allow_smem(kern, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * wpb, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <int ST> int inner_blocks_per_sm_impl(int scheme, int wpb) {
+  switch (scheme) {
+    case SC_DUGKS:
+      return inner_blocks_per_sm_scheme<SC_DUGKS, ST>(wpb);
+    case SC_BKG_FV:
+      return inner_blocks_per_sm_scheme<SC_BKG_FV, ST>(wpb);
+    case SC_BKG_FD:
+      return inner_blocks_per_sm_scheme<SC_BKG_FD, ST>(wpb);
+    default:
+      return inner_blocks_per_sm_scheme<SC_CFREE, ST>(wpb);
+  }
 }
 
 template <int ST>

@@ -2,9 +2,11 @@
 strip edges of both lane layouts (30 columns per strip with one column per
 lane in FP64, 60 with two in FP32), random heights, uniform or randomly
 stretched spacing, random boundary kinds and segments on each side, random
-launch shapes, both schemes and the upwind collision-free face.  FP64 to
-relative 1e-12 and FP32-deviation storage to 1e-6 of max |f_tilde| after
-20 steps."""
+launch shapes, both schemes and the upwind collision-free face, and for half
+of the configurations a velocity model with RT drawn log-uniformly from
+[0.1, 3] (lattice speed c = sqrt(3 RT) != 1; wall and free-stream speeds
+scaled by c).  FP64 to relative 1e-12 and FP32-deviation storage to 1e-6 of
+max |f_tilde| after 20 steps."""
 import numpy as np
 import pytest
 
@@ -61,8 +63,12 @@ def _config(k):
     bc = [per if per_x else _side(rng, yf[-1], 0.0), per if per_x else _side(rng, yf[-1], 0.0),
           per if per_y else _side(rng, xf[-1], 0.0), per if per_y else _side(rng, xf[-1], 0.04)]
     scheme = str(rng.choice(["dugks", "bkg", "cfree_upwind"], p=[0.45, 0.45, 0.1]))
-    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=W.RT_LATTICE, tau=float(rng.uniform(0.002, 0.05)),
-                dt=W.cfl_dt(xf, yf, float(rng.uniform(0.2, 0.8))), scheme=scheme, bc=bc)
+    rng_rt = np.random.default_rng(5000 + k)
+    rt = W.RT_LATTICE if rng_rt.random() < 0.5 else float(10 ** rng_rt.uniform(-1, np.log10(3)))
+    c = np.sqrt(3 * rt)
+    bc = [[(kind, s0, s1, rho, ux * c, uy * c) for (kind, s0, s1, rho, ux, uy) in side] for side in bc]
+    case = dict(nx=nx, ny=ny, xf=xf, yf=yf, RT=rt, tau=float(rng.uniform(0.002, 0.05)) / c,
+                dt=W.cfl_dt(xf, yf, float(rng.uniform(0.2, 0.8)), rt), scheme=scheme, bc=bc)
     launch = dict(strip_rows=int(rng.choice([1, 2, 3, 5, 8, 16, 33])),
                   warps_per_block=int(rng.choice([1, 2, 4, 8])), blocks=int(rng.choice([0, 0, 3])))
     return case, launch, int(rng.integers(1 << 30))

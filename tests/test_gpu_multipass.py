@@ -1,0 +1,126 @@
+"""The multi-pass FP64 step with face arrays, and the upwind-cell
+reconstruction it carries (Sec 2.4).
+
+Parity: with the linear reconstruction the multi-pass step matches the FP64
+oracle to relative 1e-12 (and the fused kernel) on periodic, walled,
+free-stream and symmetry cases; with the upwind-cell reconstruction it
+matches the oracle's upwind-cell step to 1e-12.  Measurement: the numerical
+viscosity of the two reconstructions on the Taylor-Green decay of Sec 3.1
+(N = 32 and 64, DUGKS and BKG), from the decay rate, with the collision-free
+upwind face of Eq. cfd2 beside it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dv():
+    from paper_1511_00242_gb300 import build
+    build.build()
+    import paper_1511_00242_gb300 as dv
+    return dv
+
+
+def _cases():
+    tg, _ = W.taylor_green_box(48, scheme="dugks")
+    tgs = dict(W.taylor_green_box(40, scheme="bkg")[0])
+    tgs["xf"] = W.tanh_faces(40, 0.0, 2 * math.pi, 0.8)  # stretched periodic
+    tgs["dt"] = W.cfl_dt(tgs["xf"], tgs["yf"], 0.5)
+    cav, _ = W.cavity(37, Re=200, scheme="dugks", stretch_beta=1.3, kind="diffuse")
+    box = W.cavity_four_lids(33, 26, scheme="bkg")
+    plate, _ = W.flat_plate(nx_up=8, nx_plate=26, ny=30, scheme="dugks", Re_L=2e3)
+    cf, _ = W.taylor_green_box(36, scheme="cfree_upwind")
+    return [tg, tgs, cav, box, plate, cf]
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("k", range(len(CASES)))
+@pytest.mark.parametrize("recon", ["linear", "upwind_cell"])
+def test_multipass_matches_oracle(dv, k, recon):
+    case = dict(CASES[k], recon=recon)
+    fields, delta = W.random_state(case, 60 + k, amp_neq=1e-3)
+    o = O.step(case, O.init_equilibrium(case, *fields) + delta, 30)
+    with dv.Solver(case, precision="f64", path="multipass") as s:
+        s.init_equilibrium(*fields)
+        s.init_f(s.get_f() + delta)
+        l0 = s.launch_count()
+        s.step(30)
+        assert s.launch_count() - l0 == 30 * 6
+        g = s.get_f()
+    assert float(np.max(np.abs(g - o) / np.abs(o))) < 1e-12
+    if recon == "linear":
+        with dv.Solver(case, precision="f64") as s:  # the fused kernel, same problem
+            s.init_equilibrium(*fields)
+            s.init_f(s.get_f() + delta)
+            s.step(30)
+            assert float(np.max(np.abs(s.get_f() - g) / np.abs(g))) < 1e-13
+
+
+def test_upwind_cell_selects_the_multipass_path_and_rejects_others(dv):
+    case = dict(CASES[0], recon="upwind_cell")
+    with dv.Solver(case, precision="f64") as s:  # path chosen by the reconstruction
+        s.init_equilibrium(*W.random_state(case, 1)[0])
+        l0 = s.launch_count()
+        s.step(2)
+        assert s.launch_count() - l0 == 12
+    for kw in (dict(precision="f32_dev"), dict(precision="bf16_dev")):
+        with pytest.raises(dv.DvbeError) as e:
+            dv.Solver(case, **kw)
+        assert e.value.status == dv.DVBE_ERR_UNSUPPORTED
+    with pytest.raises(dv.DvbeError) as e:
+        dv.Solver(dict(case, scheme="cfree_central"), precision="f64")
+    assert e.value.status == dv.DVBE_ERR_UNSUPPORTED
+    with pytest.raises(dv.DvbeError) as e:
+        dv.Batch([case], precision="f64")
+    assert e.value.status == dv.DVBE_ERR_UNSUPPORTED
+
+
+def _decay_viscosity(case, u, v, t):
+    """nu from the amplitude of the Taylor-Green mode at time t (Sec 3.1)."""
+    ua, va = W.taylor_green_paper_analytic(case, 0.0)
+    amp = (np.sum(u * ua) + np.sum(v * va)) / (np.sum(ua ** 2) + np.sum(va ** 2))
+    return -math.log(amp) / (8 * math.pi ** 2 * t)
+
+
+def _viscosity_excess(dv, n, scheme, recon, ratio):
+    case, fields, d, tc = W.taylor_green_paper(n, scheme, dt_over_tau=ratio)
+    case = dict(case, recon=recon)
+    steps = int(round(0.25 * tc / case["dt"]))
+    with dv.Solver(case, precision="f64", path="multipass") as s:
+        s.set_launch(graph_chunk=1000)
+        s.init_chapman_enskog(*fields, d)
+        s.step(steps)
+        _, u, v = s.moments()
+    e = _decay_viscosity(case, u, v, steps * case["dt"]) / case["nu"] - 1
+    print(f"numerical viscosity {scheme} {recon} N={n} dt/tau={ratio:g}: nu_eff/nu - 1 = {e:.4f}")
+    return e
+
+
+def test_numerical_viscosity_of_the_reconstructions(dv):
+    """At the fixed nu of Sec 3.1 the linear reconstruction's excess
+    viscosity is below 1% at N = 32 and falls at second order; the
+    upwind-cell one-sided gradient adds a dissipation of order dx^3 (the
+    Fromm scheme's), large at N = 32 and falling eightfold per halving of
+    dx; the collision-free face of Eq. cfd2 adds a viscosity that grows in
+    proportion to dt/tau."""
+    out = {}
+    for scheme in ("dugks", "bkg"):
+        for recon in ("linear", "upwind_cell"):
+            for n in (32, 64):
+                out[(scheme, recon, n)] = _viscosity_excess(dv, n, scheme, recon, 2.0)
+        for n in (32, 64):
+            assert abs(out[(scheme, "linear", n)]) < 0.01
+        assert 2.5 < out[(scheme, "linear", 32)] / out[(scheme, "linear", 64)] < 6.0
+        assert 6.0 < out[(scheme, "upwind_cell", 32)] / out[(scheme, "upwind_cell", 64)] < 10.0
+        assert abs(_viscosity_excess(dv, 64, scheme, "linear", 4.0)) < 0.02
+    for recon in ("linear", "upwind_cell"):
+        up = [_viscosity_excess(dv, 64, "cfree_upwind", recon, r) for r in (2.0, 4.0)]
+        assert up[0] > 0.4 and 1.6 < up[1] / up[0] < 2.4

@@ -126,6 +126,25 @@ def test_cavity(dv, scheme, kind, beta):
 
 
 @pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+@pytest.mark.parametrize("kind", ["wall", "diffuse"])
+def test_four_lid_box_corners(dv, scheme, kind):
+    """All four walls moving (every corner ghost in use), tanh mesh: FP64
+    parity, and the 180-degree rotation symmetry of the problem kept to
+    rounding."""
+    case = W.cavity_four_lids(75, 43, scheme=scheme, kind=kind)
+    fields = W.rotation_symmetric_state(case, 4)
+    g, o = run_pair(dv, case, 100, fields=fields, launch=dict(strip_rows=8))
+    assert rel_err(g, o) < TOL64
+    with dv.Solver(case) as s:
+        s.set_launch(strip_rows=8)
+        s.init_equilibrium(*fields)
+        s.step(100)
+        r, u, v = s.moments()
+    R = lambda a: a[::-1, ::-1]
+    assert np.max(np.abs(r - R(r))) < 1e-13 and np.max(np.abs(u + R(u))) < 1e-13
+
+
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
 def test_flat_plate(dv, scheme):
     """Inflow (W, N), outflow (E), symmetry + wall segments (S), stretched both ways."""
     case, fields = W.flat_plate(nx_up=12, nx_plate=40, ny=26, scheme=scheme)
