@@ -1,0 +1,84 @@
+"""Lid-driven cavity at Re = 1000 run to steady state (Sec 3.2): 256^2
+uniform and tanh-clustered (beta = 1.5 toward all walls) meshes, lid
+U = 0.1 c, CFL 0.5, DUGKS and BKG, FP64 and FP32-deviation storage, stepped
+until the FP64 velocity residual between checks 1000 steps apart falls below
+1e-7.
+
+Recorded per run: steps to convergence and the drift of the total mass.
+Held to: convergence within the step limit; FP64 mass conserved to 1e-10;
+the FP32-deviation steady state within 10% of the discretisation error of
+the FP64 one, the latter estimated by the difference between the DUGKS and
+BKG steady states on the same mesh (both second-order schemes; the Ghia
+reference data the paper compares with are not available)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LIMIT = {False: 1_500_000, True: 4_000_000}  # steps, uniform / tanh
+
+
+@pytest.fixture(scope="module")
+def dv():
+    from paper_1511_00242_gb300 import build
+    build.build()
+    import paper_1511_00242_gb300 as dv
+    return dv
+
+
+_RUNS = {}
+
+
+def run(dv, scheme, stretched, precision):
+    key = (scheme, stretched, precision)
+    if key in _RUNS:
+        return _RUNS[key]
+    case, fields = W.cavity(256, Re=1000, U=0.1, cfl=0.5, scheme=scheme,
+                            stretch_beta=1.5 if stretched else None)
+    with dv.Solver(case, precision=precision) as s:
+        s.set_launch(strip_rows=16, graph_chunk=500)
+        s.init_equilibrium(*fields)
+        m0 = s.conserved()[0]
+        s.residual()
+        r, steps = math.inf, 0
+        while r >= 1e-7 and steps < LIMIT[stretched]:
+            s.step(1000)
+            steps += 1000
+            r = s.residual()
+        m1 = s.conserved()[0]
+        _, u, v = s.moments()
+    res = dict(r=r, steps=steps, t=steps * case["dt"], drift=abs(m1 - m0) / m0, u=u, v=v)
+    print(f"cavity Re1000 256^2 {'tanh' if stretched else 'uniform'} {scheme} {precision}: "
+          f"R={r:.2e} after {steps} steps (t = {res['t']:.0f}), mass drift {res['drift']:.1e}")
+    _RUNS[key] = res
+    return res
+
+
+def _rel(u1, v1, u0, v0):
+    return float(np.sqrt(np.sum((u1 - u0) ** 2 + (v1 - v0) ** 2) / np.sum(u0 ** 2 + v0 ** 2)))
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_fp64_reaches_steady_state(dv, scheme, stretched):
+    r = run(dv, scheme, stretched, "f64")
+    assert r["r"] < 1e-7
+    assert r["drift"] < 1e-10
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+@pytest.mark.parametrize("scheme", ["dugks", "bkg"])
+def test_fp32_deviation_steady_state_within_bar(dv, scheme, stretched):
+    r32 = run(dv, scheme, stretched, "f32_dev")
+    assert r32["r"] < 1e-7
+    r64 = run(dv, scheme, stretched, "f64")
+    other = run(dv, "bkg" if scheme == "dugks" else "dugks", stretched, "f64")
+    e_p = _rel(r32["u"], r32["v"], r64["u"], r64["v"])
+    e_d = _rel(other["u"], other["v"], r64["u"], r64["v"])
+    print(f"  {scheme} {'tanh' if stretched else 'uniform'}: FP32-dev vs FP64 {e_p:.2e}, "
+          f"DUGKS vs BKG (FP64) {e_d:.2e}, ratio {e_p / e_d:.3f}, FP32-dev mass drift {r32['drift']:.1e}")
+    assert e_p < 0.1 * e_d
