@@ -53,6 +53,9 @@ def args_():
                    help="print the cavity stability map (max stable dt/tau against CFL) and exit")
     p.add_argument("--launch", default=None,
                    help="strip_rows,warps_per_block,blocks for the headline solver (skips its autotune)")
+    p.add_argument("--accuracy-sizes", default="256,512",
+                   help="mesh sides of the accuracy check of the headline mode (1024 adds ~4 min of FP64)")
+    p.add_argument("--batch-steps", type=int, default=2000)
     return p.parse_args()
 
 
@@ -164,35 +167,48 @@ def time_steps(dv, s, stream, torch, K):
     return e0.elapsed_time(e1) / 1e3, s.launch_count() - l0
 
 
-def batched_vs_loop(dv, torch, steps=200, chunk=50, ncases=512):
-    """The batched workload (512 cases from seed 1511, half Taylor-Green and
-    half cavities, sides 32..512, both schemes, FP32): one persistent launch
-    per scheme per step over all cases (graphs of `chunk` steps, launch shape
-    from the batch autotuner) against a loop over the cases, each stepped by
-    its own solver with the same launch shape and graphs.  Cases that diverge
-    are excluded from both sides."""
+def batched_vs_loop(dv, torch, steps=2000, chunk=50, ncases=512, precision="f32_dev"):
+    """The batched workload: 512 cases from seed 1511 (half Taylor-Green, half
+    cavities, sides 32..512, both schemes), FP32 arithmetic with FP32-deviation
+    storage, `steps` steps in CUDA graphs of `chunk` steps.  The batched form
+    is one persistent launch per scheme per step over all cases, its launch
+    shape from the batch autotuner; the per-case loop steps each case with its
+    own solver, each with its own autotuned launch shape and the same graphs.
+    Cases that diverge in the batched run are excluded from both sides and
+    listed by index.  The accuracy line is the first Taylor-Green case of the
+    batch: its error against the FP64 path over the same steps, against the
+    FP64 path's own error against the analytic decay."""
     cases = W.batched_cases(ncases, seed=1511)
     cells = np.array([c["nx"] * c["ny"] for c, _ in cases], dtype=np.float64)
-    b = dv.Batch([c for c, _ in cases], precision="f32")
+    b = dv.Batch([c for c, _ in cases], precision=precision)
     for k, (c, f) in enumerate(cases):
         b.init_equilibrium(k, *f)
-    tuned = b.autotune(2)
-    b.step(chunk, graph_chunk=chunk)  # warm-up and graph capture
+    tuned = b.autotune(10)
+    b.step(chunk, graph_chunk=chunk)  # graph capture
+    for k, (c, f) in enumerate(cases):
+        b.init_equilibrium(k, *f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.step(steps, graph_chunk=chunk)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     ok = np.array([b.case_status(k) == 0 for k in range(ncases)])
-    launch = {"strip_rows": None}
+    itg = next(k for k, (c, _) in enumerate(cases) if "taylor" in c["name"] and ok[k])
+    _, ub, vb = b.moments(itg)
     b.close()
-    solvers = []
+    solvers, shapes = [], {}
     for k, (c, f) in enumerate(cases):
-        s = dv.Solver(c, precision="f32")
-        s.set_launch(strip_rows=32, warps_per_block=4, graph_chunk=chunk)
+        s = dv.Solver(c, precision=precision)
         s.init_equilibrium(*f)
-        s.step_async(chunk)
+        s.autotune(10)
+        s.set_launch(graph_chunk=chunk)
+        l = s.get_launch()
+        shapes[(l["strip_rows"], l["warps_per_block"], l["blocks"] > 0)] = \
+            shapes.get((l["strip_rows"], l["warps_per_block"], l["blocks"] > 0), 0) + 1
+        s.step_async(chunk)  # graph capture
         solvers.append(s)
+    for s, (c, f) in zip(solvers, cases):
+        s.init_equilibrium(*f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k, s in enumerate(solvers):
@@ -203,28 +219,44 @@ def batched_vs_loop(dv, torch, steps=200, chunk=50, ncases=512):
     tl = time.perf_counter() - t0
     for s in solvers:
         s.close()
+    # accuracy of the sampled Taylor-Green case
+    c, f = cases[itg]
+    with dv.Solver(c, precision="f64") as s:
+        s.set_launch(graph_chunk=chunk)
+        s.init_equilibrium(*f)
+        s.step(steps)
+        _, u64, v64 = s.moments()
+    ua, va = W.taylor_green_box_analytic(c, steps * c["dt"])
+    ed = float(np.sqrt(np.sum((u64 - ua) ** 2 + (v64 - va) ** 2) / np.sum(ua ** 2 + va ** 2)))
+    ep = float(np.sqrt(np.sum((ub - u64) ** 2 + (vb - v64) ** 2) / np.sum(u64 ** 2 + v64 ** 2)))
     work = float(np.sum(cells[ok])) * steps
-    return {"cases": ncases, "diverged": int((~ok).sum()), "steps": steps, "graph_chunk": chunk,
+    return {"cases": ncases, "precision": precision, "steps": steps, "graph_chunk": chunk,
+            "diverged": [int(k) for k in np.nonzero(~ok)[0]],
             "cells_total": int(cells.sum()), "batched_MLUPS": work / tb / 1e6,
             "per_case_loop_MLUPS": work / tl / 1e6, "speedup": tl / tb,
-            "batched_autotune_ms_per_step": tuned}
+            "batched_autotune_ms_per_step": tuned,
+            "per_case_launch_shapes": {f"{h}x{w}{' persistent' if p else ''}": n
+                                       for (h, w, p), n in sorted(shapes.items())},
+            "accuracy_sampled_case": {"case": c["name"] + f" ({c['scheme']}, Re {c['Re']:.0f}, CFL {c['cfl']:.2f})",
+                                      "E_vs_fp64": ep, "E_fp64_vs_analytic": ed, "ratio": ep / ed,
+                                      "bar": 0.1}}
 
 
 _FP64_REF = {}
 
 
-def accuracy(dv, scheme, precision, n=256):
+def accuracy_at(dv, scheme, precision, n):
     """Error of `precision` against the FP64 path (E_p) and of the FP64 path
     against the analytic decay (E_d): Taylor-Green n^2, dt/tau = 10, run to
     10% decay of the velocity; relative L2 norms of the velocity field.  The
-    FP64 run of a scheme is made once and reused."""
+    FP64 run of a scheme and size is made once and reused."""
     case, fields = W.taylor_green_box(n, u0=0.01, cfl=0.5, scheme=scheme, dt_over_tau=10.0)
     steps = int(round(-math.log(0.9) / (2 * case["nu"]) / case["dt"]))
     ua, va = W.taylor_green_box_analytic(case, steps * case["dt"])
 
     def run(prec):
         with dv.Solver(case, precision=prec) as s:
-            s.set_launch(strip_rows=8, graph_chunk=200)
+            s.set_launch(strip_rows=16 if n <= 512 else 32, graph_chunk=200)
             s.init_equilibrium(*fields)
             s.step(steps)
             return s.moments()
@@ -235,8 +267,43 @@ def accuracy(dv, scheme, precision, n=256):
     _, up, vp = run(precision)
     ed = float(np.sqrt(np.sum((u64 - ua) ** 2 + (v64 - va) ** 2) / np.sum(ua ** 2 + va ** 2)))
     ep = float(np.sqrt(np.sum((up - u64) ** 2 + (vp - v64) ** 2) / np.sum(u64 ** 2 + v64 ** 2)))
-    return {"case": f"taylor-green {n}x{n}, dt/tau=10, {steps} steps (10% decay), {scheme.upper()}",
-            "E_vs_fp64": ep, "E_fp64_vs_analytic": ed, "ratio": ep / ed, "bar": 0.1}
+    return {"n": n, "steps": steps, "E_vs_fp64": ep, "E_fp64_vs_analytic": ed, "ratio": ep / ed}
+
+
+def accuracy(dv, scheme, precision, sizes=(256,), target_n=4096):
+    """accuracy_at over `sizes`; with two or more sizes the trend of the ratio
+    E_p / E_d is fitted as a power of n over the last two and extrapolated to
+    the timed mesh (E_d falls as n^-2 while storage rounding accumulates over
+    steps that grow as n^2)."""
+    pts = [accuracy_at(dv, scheme, precision, n) for n in sizes]
+    first = pts[0]
+    out = {"case": f"taylor-green n^2, dt/tau=10, to 10% decay, {scheme.upper()}",
+           "E_vs_fp64": first["E_vs_fp64"], "E_fp64_vs_analytic": first["E_fp64_vs_analytic"],
+           "ratio": first["ratio"], "n": first["n"], "bar": 0.1}
+    if len(pts) >= 2:
+        a, b = pts[-2], pts[-1]
+        p = math.log(b["ratio"] / a["ratio"]) / math.log(b["n"] / a["n"]) if a["ratio"] > 0 and b["ratio"] > 0 else None
+        out["trend"] = {"points": pts, "exponent": p,
+                        f"ratio_at_{target_n}_extrapolated":
+                            (b["ratio"] * (target_n / b["n"]) ** p) if p is not None else None}
+    return out
+
+
+def case_throughput(dv, stream, torch, case, fields, precision, steps, peak):
+    """MLUPS and HBM fraction of one workload (autotuned launch shape)."""
+    s = dv.Solver(case, precision=precision, stream=stream.cuda_stream)
+    try:
+        s.init_equilibrium(*fields)
+        s.autotune(10)
+        s.step(5)
+        t, _ = time_steps(dv, s, stream, torch, steps)
+        cells = case["nx"] * case["ny"]
+        ach = BYTES_PER_CELL[precision] * cells / (t / steps) / 1e9
+        return {"MLUPS": cells * steps / t / 1e6, "hbm_GBs": ach, "hbm_frac": ach / peak,
+                "launch": s.get_launch(), "cells": cells,
+                "buffers_MB": BYTES_PER_CELL[precision] // 2 * cells / 1e6}
+    finally:
+        s.close()
 
 
 def stability_map(meshes=(32, 64), cfls=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.05), iters=10, t_end=100.0):
@@ -368,21 +435,30 @@ def main():
         h, w, b = (int(x) for x in a.launch.split(","))
         s.set_launch(strip_rows=h, warps_per_block=w, blocks=b)
     elif not a.no_autotune:
-        tuned_ms = s.autotune(3)
+        tuned_ms = s.autotune(10)
     launch = s.get_launch()
-    s.step(a.warmup)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # clocks are sampled from the start of the warm-up, which runs for at
+    # least half a second, to the end of the timed steps, so that a short
+    # timed region still has samples under the same load
     clocks = Clocks(local)
-    barrier()
     clocks.start()
+    t_w = time.perf_counter()
+    s.step(a.warmup)
+    while time.perf_counter() - t_w < 0.5:
+        s.step(50)
+    barrier()
+    t_w = time.perf_counter() - t_w
     t, launches = time_steps(dv, s, stream, torch, a.steps)
     barrier()
     ck = clocks.stop()
+    if ck is not None:
+        ck["window"] = f"warm-up ({t_w:.2f} s, same steps) and the {a.steps} timed steps"
     t = max_over_ranks(t, world, "cuda")
     value = job_mlups(world, cells, a.steps, t)
     per_launch = t / a.steps
@@ -419,7 +495,7 @@ def main():
             s2 = dv.Solver(c2, precision=prec, stream=stream.cuda_stream)
             s2.init_equilibrium(*fl2)
             if not a.no_autotune:
-                s2.autotune(2)
+                s2.autotune(3 if prec == "f64" else 10)
             s2.step(3)
             k2 = 60 if prec != "f64" else 20
             t2, _ = time_steps(dv, s2, stream, torch, k2)
@@ -432,9 +508,20 @@ def main():
             if prec != "f64":
                 a2 = accuracy(dv, scheme, prec)
                 extras[f"{scheme}_{prec}"]["accuracy_ratio"] = a2["ratio"]
-        extras["batched_vs_per_case_loop"] = batched_vs_loop(dv, torch)
+        # the other workloads of the paper's tests at their stated sizes (Sec 3.2, 3.3)
+        for scheme in ("dugks", "bkg"):
+            c3, fl3 = W.cavity(2048, Re=5000, cfl=0.5, scheme=scheme)
+            extras[f"cavity_2048_re5000_{scheme}_f32_dev"] = case_throughput(
+                dv, stream, torch, c3, fl3, "f32_dev", 60, peak)
+            c4, fl4 = W.flat_plate(nx_up=170, nx_plate=342, ny=256, scheme=scheme)
+            extras[f"plate_512x256_{scheme}_f32_dev"] = dict(case_throughput(
+                dv, stream, torch, c4, fl4, "f32_dev", 400, peak),
+                note="4.7 MB buffers, resident in L2: not HBM-bound")
+        extras["batched_vs_per_case_loop"] = batched_vs_loop(dv, torch, steps=a.batch_steps)
     s.close()
-    acc = accuracy(dv, a.scheme, a.precision) if rank == 0 and a.precision != "f64" else None
+    sizes = tuple(int(x) for x in a.accuracy_sizes.split(",") if x)
+    acc = (accuracy(dv, a.scheme, a.precision, sizes=sizes, target_n=a.n)
+           if rank == 0 and a.precision != "f64" and sizes else None)
 
     fbytes = BYTES_PER_CELL[a.precision] // 2 * cells
     if rank == 0:
