@@ -246,3 +246,95 @@ def l2_error_u(case: dict, f_tilde: np.ndarray, ua, va) -> float:
     e = ctypes.c_double()
     _check(lib().orc_l2_error_u(P.ref(), _dp(f), _dp(ua), _dp(va), ctypes.byref(e)), "l2_error_u")
     return e.value
+
+
+# ---------------------------------------------------------------- quad meshes
+#
+# A curvilinear structured mesh is a case dict with vertex arrays instead of
+# face coordinates:
+#
+#     qcase = dict(nx=, ny=, X=[(ny+1), (nx+1)], Y=[(ny+1), (nx+1)], RT=, tau=, dt=,
+#                  scheme=, recon=, bc=[W, E, S, N])
+#
+# cell (i, j) has the vertices (i, j), (i+1, j), (i+1, j+1), (i, j+1),
+# counter-clockwise.
+
+class _QuadProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("X", _DP), ("Y", _DP),
+                ("RT", ctypes.c_double), ("tau", ctypes.c_double), ("dt", ctypes.c_double),
+                ("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("nbc", ctypes.c_int * 4),
+                ("bc", ctypes.POINTER(_Seg) * 4)]
+
+
+class QuadProblem:
+    def __init__(self, case: dict):
+        self.nx, self.ny = int(case["nx"]), int(case["ny"])
+        self.X = np.ascontiguousarray(case["X"], dtype=np.float64)
+        self.Y = np.ascontiguousarray(case["Y"], dtype=np.float64)
+        assert self.X.shape == (self.ny + 1, self.nx + 1) == self.Y.shape
+        self._segs = []
+        s = _QuadProblem()
+        s.nx, s.ny = self.nx, self.ny
+        s.X, s.Y = _dp(self.X), _dp(self.Y)
+        s.RT, s.tau, s.dt = float(case["RT"]), float(case["tau"]), float(case["dt"])
+        s.scheme = SCHEMES[case.get("scheme", "dugks")]
+        s.recon = RECONS[case.get("recon", "linear")]
+        for side in range(4):
+            segs = case["bc"][side]
+            arr = (_Seg * len(segs))()
+            for k, seg in enumerate(segs):
+                kind, s0, s1, rho, ux, uy = seg
+                arr[k] = _Seg(KINDS[kind], s0, s1, rho, ux, uy)
+            self._segs.append(arr)
+            s.nbc[side] = len(segs)
+            s.bc[side] = ctypes.cast(arr, ctypes.POINTER(_Seg))
+        self.s = s
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _quad_lib():
+    L = lib()
+    for name in ("orc_quad_geometry", "orc_quad_step", "orc_quad_conserved", "orc_quad_dt_from_cfl"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+def quad_geometry(case: dict):
+    """Cell centres and volumes, each [ny, nx]."""
+    P = QuadProblem(case)
+    xc, yc, vol = (np.zeros((P.ny, P.nx)) for _ in range(3))
+    _check(_quad_lib().orc_quad_geometry(P.ref(), _dp(xc), _dp(yc), _dp(vol)), "orc_quad_geometry")
+    return xc, yc, vol
+
+
+def quad_step(case: dict, f_tilde: np.ndarray, nsteps: int) -> np.ndarray:
+    P = QuadProblem(case)
+    f = np.array(f_tilde, dtype=np.float64, order="C", copy=True)
+    assert f.shape == (9, P.ny, P.nx)
+    _check(_quad_lib().orc_quad_step(P.ref(), _dp(f), ctypes.c_longlong(nsteps)), "orc_quad_step")
+    return f
+
+
+def quad_conserved(case: dict, f_tilde: np.ndarray) -> np.ndarray:
+    P = QuadProblem(case)
+    out = np.zeros(3)
+    _check(_quad_lib().orc_quad_conserved(P.ref(), _dp(_f2(f_tilde)), _dp(out)), "orc_quad_conserved")
+    return out
+
+
+def quad_dt_from_cfl(case: dict, cfl: float) -> float:
+    P = QuadProblem(case)
+    dt = ctypes.c_double()
+    _check(_quad_lib().orc_quad_dt_from_cfl(P.ref(), ctypes.c_double(cfl), ctypes.byref(dt)),
+           "orc_quad_dt_from_cfl")
+    return dt.value
+
+
+def quad_init_equilibrium(case: dict, rho, ux, uy) -> np.ndarray:
+    """f_tilde = f_eq(rho, u) cell by cell (pointwise: the mesh plays no part)."""
+    nx, ny = int(case["nx"]), int(case["ny"])
+    flat = dict(nx=nx, ny=ny, xf=np.arange(nx + 1.0), yf=np.arange(ny + 1.0), RT=case["RT"],
+                tau=case["tau"], dt=case["dt"], bc=[[("periodic", -1e300, 1e300, 1, 0, 0)]] * 4)
+    return init_equilibrium(flat, rho, ux, uy)

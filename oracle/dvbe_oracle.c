@@ -1004,3 +1004,466 @@ int orc_l2_error_u(const orc_problem *p, const double *f_tilde, const double *ua
   *eu = sqrt(num) / sqrt(den);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Curvilinear structured meshes (readings in dvbe_oracle.h)            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int nx, ny, per_x, per_y;
+  double Px[2], Py[2]; /* translation from side W to E, from S to N (periodic) */
+  double *cx, *cy;     /* padded centres, i = -2 .. nx+1, j = -2 .. ny+1 */
+  double *vol;         /* [ny][nx] */
+  /* x-faces [ny][nx+1], y-faces [ny+1][nx]: midpoint, unit normal, area */
+  double *xbx, *xby, *xnx, *xny, *xA;
+  double *ybx, *yby, *ynx, *yny, *yA;
+  const orc_bc_segment **segW, **segE, **segS, **segN;
+} qgeom;
+
+#define QIDX(g, i, j) ((size_t)((j) + 2) * ((g)->nx + 4) + (size_t)((i) + 2))
+#define QV(p, i, j) ((size_t)(j) * ((p)->nx + 1) + (size_t)(i))
+
+static void qgeom_free(qgeom *g) {
+  double *arrs[] = {g->cx, g->cy, g->vol, g->xbx, g->xby, g->xnx, g->xny, g->xA,
+                    g->ybx, g->yby, g->ynx, g->yny, g->yA};
+  for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
+  free((void *)g->segW);
+  free((void *)g->segE);
+  free((void *)g->segS);
+  free((void *)g->segN);
+  memset(g, 0, sizeof(*g));
+}
+
+/* Mirror of point (x, y) across the line through (bx, by) with unit normal n. */
+static void mirror(double x, double y, double bx, double by, double nx_, double ny_,
+                   double *mx, double *my) {
+  const double s = (x - bx) * nx_ + (y - by) * ny_;
+  *mx = x - 2.0 * s * nx_;
+  *my = y - 2.0 * s * ny_;
+}
+
+static int axis_normal(double nx_, double ny_) {
+  return fabs(fabs(nx_) - 1.0) <= 1e-12 || fabs(fabs(ny_) - 1.0) <= 1e-12;
+}
+
+static int qgeom_build(const orc_quad_problem *p, qgeom *g) {
+  memset(g, 0, sizeof(*g));
+  if (!p || p->nx < 2 || p->ny < 2 || !p->X || !p->Y) return ORC_EINVAL;
+  if (!(p->RT > 0.0) || !(p->tau > 0.0) || !(p->dt > 0.0)) return ORC_EINVAL;
+  if (p->scheme < ORC_DUGKS || p->scheme > ORC_CFREE_CENTRAL) return ORC_EINVAL;
+  if (p->recon != ORC_RECON_LINEAR && p->recon != ORC_RECON_UPWIND_CELL) return ORC_EINVAL;
+  int per[4];
+  for (int s = 0; s < 4; ++s) {
+    if (p->nbc[s] < 1 || !p->bc[s]) return ORC_EINVAL;
+    per[s] = 0;
+    for (int k = 0; k < p->nbc[s]; ++k) {
+      if (!kind_valid(p->bc[s][k].kind)) return ORC_EINVAL;
+      if (p->bc[s][k].kind == ORC_BC_PERIODIC) per[s] = 1;
+    }
+    if (per[s] && p->nbc[s] != 1) return ORC_EINVAL;
+  }
+  if (per[ORC_SIDE_W] != per[ORC_SIDE_E] || per[ORC_SIDE_S] != per[ORC_SIDE_N]) return ORC_EINVAL;
+  const int nx = p->nx, ny = p->ny;
+  g->nx = nx;
+  g->ny = ny;
+  g->per_x = per[ORC_SIDE_W];
+  g->per_y = per[ORC_SIDE_S];
+  const size_t np = (size_t)(nx + 4) * (ny + 4), nfx = (size_t)(nx + 1) * ny, nfy = (size_t)nx * (ny + 1);
+  g->cx = calloc(np, sizeof(double));
+  g->cy = calloc(np, sizeof(double));
+  g->vol = calloc((size_t)nx * ny, sizeof(double));
+  double **fx[5] = {&g->xbx, &g->xby, &g->xnx, &g->xny, &g->xA};
+  double **fy[5] = {&g->ybx, &g->yby, &g->ynx, &g->yny, &g->yA};
+  for (int q = 0; q < 5; ++q) {
+    *fx[q] = calloc(nfx, sizeof(double));
+    *fy[q] = calloc(nfy, sizeof(double));
+  }
+  g->segW = calloc(ny, sizeof(void *));
+  g->segE = calloc(ny, sizeof(void *));
+  g->segS = calloc(nx, sizeof(void *));
+  g->segN = calloc(nx, sizeof(void *));
+  if (!g->cx || !g->cy || !g->vol || !g->xA || !g->yA || !g->segW || !g->segE || !g->segS || !g->segN) {
+    qgeom_free(g);
+    return ORC_EINVAL;
+  }
+  const double *X = p->X, *Y = p->Y;
+  /* periodic translations */
+  g->Px[0] = X[QV(p, nx, 0)] - X[QV(p, 0, 0)];
+  g->Px[1] = Y[QV(p, nx, 0)] - Y[QV(p, 0, 0)];
+  g->Py[0] = X[QV(p, 0, ny)] - X[QV(p, 0, 0)];
+  g->Py[1] = Y[QV(p, 0, ny)] - Y[QV(p, 0, 0)];
+  /* cells */
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double x0 = X[QV(p, i, j)], x1 = X[QV(p, i + 1, j)], x2 = X[QV(p, i + 1, j + 1)], x3 = X[QV(p, i, j + 1)];
+      const double y0 = Y[QV(p, i, j)], y1 = Y[QV(p, i + 1, j)], y2 = Y[QV(p, i + 1, j + 1)], y3 = Y[QV(p, i, j + 1)];
+      g->cx[QIDX(g, i, j)] = 0.25 * (x0 + x1 + x2 + x3);
+      g->cy[QIDX(g, i, j)] = 0.25 * (y0 + y1 + y2 + y3);
+      const double area = 0.5 * ((x0 * y1 - x1 * y0) + (x1 * y2 - x2 * y1) + (x2 * y3 - x3 * y2) + (x3 * y0 - x0 * y3));
+      if (!(area > 0.0)) {
+        qgeom_free(g);
+        return ORC_EINVAL;
+      }
+      g->vol[(size_t)j * nx + i] = area;
+    }
+  /* faces */
+  for (int j = 0; j < ny; ++j)
+    for (int k = 0; k <= nx; ++k) {
+      const double ax = X[QV(p, k, j)], ay = Y[QV(p, k, j)], bx = X[QV(p, k, j + 1)], by = Y[QV(p, k, j + 1)];
+      const double tx = bx - ax, ty = by - ay, len = sqrt(tx * tx + ty * ty);
+      const size_t f = (size_t)j * (nx + 1) + k;
+      g->xbx[f] = 0.5 * (ax + bx);
+      g->xby[f] = 0.5 * (ay + by);
+      g->xnx[f] = ty / len;
+      g->xny[f] = -tx / len;
+      g->xA[f] = len;
+    }
+  for (int k = 0; k <= ny; ++k)
+    for (int i = 0; i < nx; ++i) {
+      const double ax = X[QV(p, i, k)], ay = Y[QV(p, i, k)], bx = X[QV(p, i + 1, k)], by = Y[QV(p, i + 1, k)];
+      const double tx = bx - ax, ty = by - ay, len = sqrt(tx * tx + ty * ty);
+      const size_t f = (size_t)k * nx + i;
+      g->ybx[f] = 0.5 * (ax + bx);
+      g->yby[f] = 0.5 * (ay + by);
+      g->ynx[f] = -ty / len;
+      g->yny[f] = tx / len;
+      g->yA[f] = len;
+    }
+  /* ghost centres: x sides over the inner rows, then y sides over the padded width */
+  for (int j = 0; j < ny; ++j) {
+    if (g->per_x) {
+      for (int l = 1; l <= 2; ++l) {
+        g->cx[QIDX(g, -l, j)] = g->cx[QIDX(g, nx - l, j)] - g->Px[0];
+        g->cy[QIDX(g, -l, j)] = g->cy[QIDX(g, nx - l, j)] - g->Px[1];
+        g->cx[QIDX(g, nx - 1 + l, j)] = g->cx[QIDX(g, l - 1, j)] + g->Px[0];
+        g->cy[QIDX(g, nx - 1 + l, j)] = g->cy[QIDX(g, l - 1, j)] + g->Px[1];
+      }
+    } else {
+      for (int side = 0; side < 2; ++side) {
+        const int i1 = side == 0 ? 0 : nx - 1, ig = side == 0 ? -1 : nx, ig2 = side == 0 ? -2 : nx + 1;
+        const size_t f = (size_t)j * (nx + 1) + (side == 0 ? 0 : nx);
+        mirror(g->cx[QIDX(g, i1, j)], g->cy[QIDX(g, i1, j)], g->xbx[f], g->xby[f], g->xnx[f], g->xny[f],
+               &g->cx[QIDX(g, ig, j)], &g->cy[QIDX(g, ig, j)]);
+        g->cx[QIDX(g, ig2, j)] = 2.0 * g->cx[QIDX(g, ig, j)] - g->cx[QIDX(g, i1, j)];
+        g->cy[QIDX(g, ig2, j)] = 2.0 * g->cy[QIDX(g, ig, j)] - g->cy[QIDX(g, i1, j)];
+      }
+    }
+  }
+  for (int i = -2; i <= nx + 1; ++i) {
+    if (g->per_y) {
+      for (int l = 1; l <= 2; ++l) {
+        g->cx[QIDX(g, i, -l)] = g->cx[QIDX(g, i, ny - l)] - g->Py[0];
+        g->cy[QIDX(g, i, -l)] = g->cy[QIDX(g, i, ny - l)] - g->Py[1];
+        g->cx[QIDX(g, i, ny - 1 + l)] = g->cx[QIDX(g, i, l - 1)] + g->Py[0];
+        g->cy[QIDX(g, i, ny - 1 + l)] = g->cy[QIDX(g, i, l - 1)] + g->Py[1];
+      }
+    } else {
+      const int ic = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+      for (int side = 0; side < 2; ++side) {
+        const int j1 = side == 0 ? 0 : ny - 1, jg = side == 0 ? -1 : ny, jg2 = side == 0 ? -2 : ny + 1;
+        const size_t f = (size_t)(side == 0 ? 0 : ny) * nx + ic;
+        mirror(g->cx[QIDX(g, i, j1)], g->cy[QIDX(g, i, j1)], g->ybx[f], g->yby[f], g->ynx[f], g->yny[f],
+               &g->cx[QIDX(g, i, jg)], &g->cy[QIDX(g, i, jg)]);
+        g->cx[QIDX(g, i, jg2)] = 2.0 * g->cx[QIDX(g, i, jg)] - g->cx[QIDX(g, i, j1)];
+        g->cy[QIDX(g, i, jg2)] = 2.0 * g->cy[QIDX(g, i, jg)] - g->cy[QIDX(g, i, j1)];
+      }
+    }
+  }
+  /* boundary segments by face centre; symmetry needs an axis-aligned face */
+  for (int j = 0; j < ny; ++j) {
+    if (g->per_x) continue;
+    const size_t fw = (size_t)j * (nx + 1), fe = fw + nx;
+    for (int k = 0; k < p->nbc[ORC_SIDE_W]; ++k)
+      if (g->xby[fw] >= p->bc[ORC_SIDE_W][k].s0 && g->xby[fw] < p->bc[ORC_SIDE_W][k].s1) {
+        g->segW[j] = &p->bc[ORC_SIDE_W][k];
+        break;
+      }
+    for (int k = 0; k < p->nbc[ORC_SIDE_E]; ++k)
+      if (g->xby[fe] >= p->bc[ORC_SIDE_E][k].s0 && g->xby[fe] < p->bc[ORC_SIDE_E][k].s1) {
+        g->segE[j] = &p->bc[ORC_SIDE_E][k];
+        break;
+      }
+    if (!g->segW[j] || !g->segE[j] || g->segW[j]->kind == ORC_BC_PERIODIC || g->segE[j]->kind == ORC_BC_PERIODIC ||
+        (g->segW[j]->kind == ORC_BC_SYMMETRY && !axis_normal(g->xnx[fw], g->xny[fw])) ||
+        (g->segE[j]->kind == ORC_BC_SYMMETRY && !axis_normal(g->xnx[fe], g->xny[fe]))) {
+      qgeom_free(g);
+      return ORC_EINVAL;
+    }
+  }
+  for (int i = 0; i < nx; ++i) {
+    if (g->per_y) continue;
+    const size_t fs = (size_t)i, fn = (size_t)ny * nx + i;
+    for (int k = 0; k < p->nbc[ORC_SIDE_S]; ++k)
+      if (g->ybx[fs] >= p->bc[ORC_SIDE_S][k].s0 && g->ybx[fs] < p->bc[ORC_SIDE_S][k].s1) {
+        g->segS[i] = &p->bc[ORC_SIDE_S][k];
+        break;
+      }
+    for (int k = 0; k < p->nbc[ORC_SIDE_N]; ++k)
+      if (g->ybx[fn] >= p->bc[ORC_SIDE_N][k].s0 && g->ybx[fn] < p->bc[ORC_SIDE_N][k].s1) {
+        g->segN[i] = &p->bc[ORC_SIDE_N][k];
+        break;
+      }
+    if (!g->segS[i] || !g->segN[i] || g->segS[i]->kind == ORC_BC_PERIODIC || g->segN[i]->kind == ORC_BC_PERIODIC ||
+        (g->segS[i]->kind == ORC_BC_SYMMETRY && !axis_normal(g->ynx[fs], g->yny[fs])) ||
+        (g->segN[i]->kind == ORC_BC_SYMMETRY && !axis_normal(g->ynx[fn], g->yny[fn]))) {
+      qgeom_free(g);
+      return ORC_EINVAL;
+    }
+  }
+  return ORC_OK;
+}
+
+/* Extrapolation factor e = ((x_g - x_1) . n) / ((x_1 - x_2) . n), n the
+ * boundary face's normal: the ratio of the distances to the wall. */
+static double qext(const qgeom *g, size_t cg, size_t c1, size_t c2, double nx_, double ny_) {
+  const double dx = g->cx[c1] - g->cx[c2], dy = g->cy[c1] - g->cy[c2];
+  return ((g->cx[cg] - g->cx[c1]) * nx_ + (g->cy[cg] - g->cy[c1]) * ny_) / (dx * nx_ + dy * ny_);
+}
+
+/* Mirror map of a symmetry face: the one of the axis its normal lies on. */
+static const int *qmir(const vset *v, double nx_) { return fabs(nx_) > 0.5 ? v->mirx : v->miry; }
+
+static void qfill_ghosts(const vset *v, const qgeom *g, double *P) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t plane = (size_t)(nx + 4) * (ny + 4);
+  double p1[9], p2[9], pg[9];
+  for (int j = 0; j < ny; ++j) {
+    for (int side = 0; side < 2; ++side) {
+      if (g->per_x) {
+        for (int l = 1; l <= 2; ++l) {
+          const int ig = side == 0 ? -l : nx - 1 + l, src = side == 0 ? nx - l : l - 1;
+          for (int a = 0; a < 9; ++a) P[a * plane + QIDX(g, ig, j)] = P[a * plane + QIDX(g, src, j)];
+        }
+        continue;
+      }
+      const int ig = side == 0 ? -1 : nx, i1 = side == 0 ? 0 : nx - 1, i2 = side == 0 ? 1 : nx - 2;
+      for (int a = 0; a < 9; ++a) {
+        p1[a] = P[a * plane + QIDX(g, i1, j)];
+        p2[a] = P[a * plane + QIDX(g, i2, j)];
+      }
+      const size_t f = (size_t)j * (nx + 1) + (side == 0 ? 0 : nx);
+      const double e = qext(g, QIDX(g, ig, j), QIDX(g, i1, j), QIDX(g, i2, j), g->xnx[f], g->xny[f]);
+      ghost_rule(v, side == 0 ? g->segW[j] : g->segE[j], e, qmir(v, g->xnx[f]), p1, p2, pg);
+      for (int a = 0; a < 9; ++a) P[a * plane + QIDX(g, ig, j)] = pg[a];
+    }
+  }
+  const int ilo = g->per_x ? -2 : -1, ihi = g->per_x ? nx + 1 : nx;
+  for (int i = ilo; i <= ihi; ++i) {
+    const int ic = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+    for (int side = 0; side < 2; ++side) {
+      if (g->per_y) {
+        for (int l = 1; l <= 2; ++l) {
+          const int jg = side == 0 ? -l : ny - 1 + l, src = side == 0 ? ny - l : l - 1;
+          for (int a = 0; a < 9; ++a) P[a * plane + QIDX(g, i, jg)] = P[a * plane + QIDX(g, i, src)];
+        }
+        continue;
+      }
+      const int jg = side == 0 ? -1 : ny, j1 = side == 0 ? 0 : ny - 1, j2 = side == 0 ? 1 : ny - 2;
+      for (int a = 0; a < 9; ++a) {
+        p1[a] = P[a * plane + QIDX(g, i, j1)];
+        p2[a] = P[a * plane + QIDX(g, i, j2)];
+      }
+      const size_t f = (size_t)(side == 0 ? 0 : ny) * nx + ic;
+      const double e = qext(g, QIDX(g, i, jg), QIDX(g, i, j1), QIDX(g, i, j2), g->ynx[f], g->yny[f]);
+      ghost_rule(v, side == 0 ? g->segS[ic] : g->segN[ic], e, qmir(v, g->ynx[f]), p1, p2, pg);
+      for (int a = 0; a < 9; ++a) P[a * plane + QIDX(g, i, jg)] = pg[a];
+    }
+  }
+}
+
+/* Gradient of field Pa at padded cell (i, j) by central differences along
+ * the two mesh lines (one-sided toward the inside at the outer layer of a
+ * non-periodic side), grad = J^-T (d_i, d_j). */
+static void qgrad(const qgeom *g, const double *Pa, int i, int j, double *gx, double *gy) {
+  int im = i - 1, ip = i + 1, jm = j - 1, jp = j + 1;
+  if (!g->per_x && i <= -1) im = i;
+  if (!g->per_x && i >= g->nx) ip = i;
+  if (!g->per_y && j <= -1) jm = j;
+  if (!g->per_y && j >= g->ny) jp = j;
+  const double pi = Pa[QIDX(g, ip, j)] - Pa[QIDX(g, im, j)];
+  const double pj = Pa[QIDX(g, i, jp)] - Pa[QIDX(g, i, jm)];
+  const double xi_ = g->cx[QIDX(g, ip, j)] - g->cx[QIDX(g, im, j)];
+  const double yi_ = g->cy[QIDX(g, ip, j)] - g->cy[QIDX(g, im, j)];
+  const double xj_ = g->cx[QIDX(g, i, jp)] - g->cx[QIDX(g, i, jm)];
+  const double yj_ = g->cy[QIDX(g, i, jp)] - g->cy[QIDX(g, i, jm)];
+  const double det = xi_ * yj_ - yi_ * xj_;
+  *gx = (pi * yj_ - yi_ * pj) / det;
+  *gy = (xi_ * pj - pi * xj_) / det;
+}
+
+/* phi(x_b - h xi) at a face with midpoint (bx, by) and unit normal n between
+ * padded cells L and R; upwind: the upwind-cell form is allowed here. */
+static void qrecon(const vset *v, const qgeom *g, const double *P, int iL, int jL, int iR, int jR,
+                   double bx, double by, double nx_, double ny_, double h, int upwind, double *out) {
+  const size_t plane = (size_t)(g->nx + 4) * (g->ny + 4);
+  const size_t L = QIDX(g, iL, jL), R = QIDX(g, iR, jR);
+  const double dx = g->cx[R] - g->cx[L], dy = g->cy[R] - g->cy[L], dn = dx * nx_ + dy * ny_;
+  const double th = ((bx - g->cx[L]) * nx_ + (by - g->cy[L]) * ny_) / dn;
+  const double ox = bx - (g->cx[L] + th * dx), oy = by - (g->cy[L] + th * dy);
+  for (int a = 0; a < 9; ++a) {
+    const double *Pa = P + a * plane;
+    const double xn = v->xi[a][0] * nx_ + v->xi[a][1] * ny_;
+    if (upwind && xn != 0.0) {
+      const int iC = xn > 0.0 ? iL : iR, jC = xn > 0.0 ? jL : jR;
+      const size_t C = QIDX(g, iC, jC);
+      double gx, gy;
+      qgrad(g, Pa, iC, jC, &gx, &gy);
+      out[a] = Pa[C] + (bx - h * v->xi[a][0] - g->cx[C]) * gx + (by - h * v->xi[a][1] - g->cy[C]) * gy;
+      continue;
+    }
+    double glx, gly, grx, gry;
+    qgrad(g, Pa, iL, jL, &glx, &gly);
+    qgrad(g, Pa, iR, jR, &grx, &gry);
+    const double gbx = (1.0 - th) * glx + th * grx, gby = (1.0 - th) * gly + th * gry;
+    const double pb = (1.0 - th) * Pa[L] + th * Pa[R] + gbx * ox + gby * oy;
+    const double corr = ((Pa[R] - Pa[L]) - (gbx * dx + gby * dy)) / dn;
+    const double gfx = gbx + corr * nx_, gfy = gby + corr * ny_;
+    out[a] = pb - h * (v->xi[a][0] * gfx + v->xi[a][1] * gfy);
+  }
+}
+
+static int qstep_once(const orc_quad_problem *p, const vset *v, const qgeom *g, double *ft,
+                      double *P, double *TP, double *FX, double *FY) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t n = (size_t)nx * ny, plane = (size_t)(nx + 4) * (ny + 4);
+  const size_t nfx = (size_t)(nx + 1) * ny, nfy = (size_t)nx * (ny + 1);
+  const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
+  double f9[9], fe[9], rho, ux, uy, val[9];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t k = (size_t)j * nx + i;
+      for (int a = 0; a < 9; ++a) f9[a] = ft[a * n + k];
+      moments_of(v, f9, &rho, &ux, &uy);
+      feq_of(v, rho, ux, uy, fe);
+      for (int a = 0; a < 9; ++a) {
+        const double tplus = ((2.0 * tau - dt) * f9[a] + 2.0 * dt * fe[a]) / (2.0 * tau + dt);
+        double phi;
+        if (p->scheme == ORC_DUGKS)
+          phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);
+        else if (p->scheme == ORC_BKG)
+          phi = tplus;
+        else
+          phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);
+        TP[a * n + k] = tplus;
+        P[a * plane + QIDX(g, i, j)] = phi;
+      }
+    }
+  qfill_ghosts(v, g, P);
+  const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;
+  for (int j = 0; j < ny; ++j)
+    for (int k = 0; k <= nx; ++k) {
+      const size_t f = (size_t)j * (nx + 1) + k;
+      const int upw = p->recon == ORC_RECON_UPWIND_CELL && (g->per_x || (k > 0 && k < nx));
+      qrecon(v, g, P, k - 1, j, k, j, g->xbx[f], g->xby[f], g->xnx[f], g->xny[f], hs, upw, val);
+      if (!g->per_x && k == 0) face_bc(v, g->segW[j], -g->xnx[f], -g->xny[f], val);
+      if (!g->per_x && k == nx) face_bc(v, g->segE[j], g->xnx[f], g->xny[f], val);
+      face_to_f(v, (const orc_problem *)&(orc_problem){.dt = p->dt, .tau = p->tau, .scheme = p->scheme}, val);
+      for (int a = 0; a < 9; ++a) FX[(size_t)a * nfx + f] = val[a];
+    }
+  for (int k = 0; k <= ny; ++k)
+    for (int i = 0; i < nx; ++i) {
+      const size_t f = (size_t)k * nx + i;
+      const int upw = p->recon == ORC_RECON_UPWIND_CELL && (g->per_y || (k > 0 && k < ny));
+      qrecon(v, g, P, i, k - 1, i, k, g->ybx[f], g->yby[f], g->ynx[f], g->yny[f], hs, upw, val);
+      if (!g->per_y && k == 0) face_bc(v, g->segS[i], -g->ynx[f], -g->yny[f], val);
+      if (!g->per_y && k == ny) face_bc(v, g->segN[i], g->ynx[f], g->yny[f], val);
+      face_to_f(v, (const orc_problem *)&(orc_problem){.dt = p->dt, .tau = p->tau, .scheme = p->scheme}, val);
+      for (int a = 0; a < 9; ++a) FY[(size_t)a * nfy + f] = val[a];
+    }
+  /* f_tilde^{n+1} = f_tilde^+ - dt/|V| sum_faces (xi . n_out) A f_face */
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t k = (size_t)j * nx + i;
+      const size_t fw = (size_t)j * (nx + 1) + i, fe_ = fw + 1, fs = (size_t)j * nx + i, fn = fs + nx;
+      for (int a = 0; a < 9; ++a) {
+        const double x0 = v->xi[a][0], x1 = v->xi[a][1];
+        const double out_flux =
+            (x0 * g->xnx[fe_] + x1 * g->xny[fe_]) * g->xA[fe_] * FX[(size_t)a * nfx + fe_] -
+            (x0 * g->xnx[fw] + x1 * g->xny[fw]) * g->xA[fw] * FX[(size_t)a * nfx + fw] +
+            (x0 * g->ynx[fn] + x1 * g->yny[fn]) * g->yA[fn] * FY[(size_t)a * nfy + fn] -
+            (x0 * g->ynx[fs] + x1 * g->yny[fs]) * g->yA[fs] * FY[(size_t)a * nfy + fs];
+        ft[a * n + k] = TP[a * n + k] - dt / g->vol[k] * out_flux;
+      }
+    }
+  return ORC_OK;
+}
+
+int orc_quad_step(const orc_quad_problem *p, double *f_tilde, long long nsteps) {
+  if (!f_tilde || nsteps < 0) return ORC_EINVAL;
+  qgeom g;
+  int rc = qgeom_build(p, &g);
+  if (rc) return rc;
+  vset v;
+  make_vset(p->RT, &v);
+  const int nx = p->nx, ny = p->ny;
+  double *P = calloc((size_t)9 * (nx + 4) * (ny + 4), sizeof(double));
+  double *TP = calloc((size_t)9 * nx * ny, sizeof(double));
+  double *FX = calloc((size_t)9 * (nx + 1) * ny, sizeof(double));
+  double *FY = calloc((size_t)9 * nx * (ny + 1), sizeof(double));
+  if (!P || !TP || !FX || !FY) rc = ORC_EINVAL;
+  for (long long s = 0; s < nsteps && !rc; ++s) rc = qstep_once(p, &v, &g, f_tilde, P, TP, FX, FY);
+  free(P);
+  free(TP);
+  free(FX);
+  free(FY);
+  qgeom_free(&g);
+  return rc;
+}
+
+int orc_quad_geometry(const orc_quad_problem *p, double *xc, double *yc, double *vol) {
+  qgeom g;
+  int rc = qgeom_build(p, &g);
+  if (rc) return rc;
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i) {
+      const size_t k = (size_t)j * p->nx + i;
+      if (xc) xc[k] = g.cx[QIDX(&g, i, j)];
+      if (yc) yc[k] = g.cy[QIDX(&g, i, j)];
+      if (vol) vol[k] = g.vol[k];
+    }
+  qgeom_free(&g);
+  return ORC_OK;
+}
+
+int orc_quad_conserved(const orc_quad_problem *p, const double *f_tilde, double *out) {
+  if (!f_tilde || !out) return ORC_EINVAL;
+  qgeom g;
+  int rc = qgeom_build(p, &g);
+  if (rc) return rc;
+  vset v;
+  make_vset(p->RT, &v);
+  const size_t n = (size_t)p->nx * p->ny;
+  double m = 0.0, jx = 0.0, jy = 0.0;
+  for (size_t k = 0; k < n; ++k)
+    for (int a = 0; a < 9; ++a) {
+      const double fa = f_tilde[a * n + k];
+      m += fa * g.vol[k];
+      jx += v.xi[a][0] * fa * g.vol[k];
+      jy += v.xi[a][1] * fa * g.vol[k];
+    }
+  out[0] = m;
+  out[1] = jx;
+  out[2] = jy;
+  qgeom_free(&g);
+  return ORC_OK;
+}
+
+int orc_quad_dt_from_cfl(const orc_quad_problem *p, double cfl, double *dt) {
+  if (!p || !dt || !(cfl > 0.0) || !(p->RT > 0.0)) return ORC_EINVAL;
+  double dmin = INFINITY;
+  for (int j = 0; j <= p->ny; ++j)
+    for (int i = 0; i <= p->nx; ++i) {
+      if (i < p->nx) {
+        const double dx = p->X[QV(p, i + 1, j)] - p->X[QV(p, i, j)], dy = p->Y[QV(p, i + 1, j)] - p->Y[QV(p, i, j)];
+        const double l = sqrt(dx * dx + dy * dy);
+        if (l < dmin) dmin = l;
+      }
+      if (j < p->ny) {
+        const double dx = p->X[QV(p, i, j + 1)] - p->X[QV(p, i, j)], dy = p->Y[QV(p, i, j + 1)] - p->Y[QV(p, i, j)];
+        const double l = sqrt(dx * dx + dy * dy);
+        if (l < dmin) dmin = l;
+      }
+    }
+  *dt = cfl * dmin / (sqrt(6.0) * sqrt(p->RT));
+  return ORC_OK;
+}

@@ -142,6 +142,61 @@ int orc_conserved(const orc_problem *p, const double *f_tilde, double *out);
 int orc_l2_error_u(const orc_problem *p, const double *f_tilde,
                    const double *ua, const double *va, double *eu);
 
+/* ---- curvilinear structured meshes (general quadrilateral cells) -------
+ * The FV form of Sec 2.2 on cells V_k with faces of any orientation: cell
+ * (i, j) has the vertices (i, j), (i+1, j), (i+1, j+1), (i, j+1) of the
+ * vertex arrays X, Y [(ny+1)][(nx+1)] (counter-clockwise).  Readings (the
+ * paper states the method for general cells but gives the reconstruction
+ * only on uniform meshes):
+ *   - cell centre: the mean of its four vertices; volume: its area;
+ *   - face: the edge between two cells, with midpoint x_b, unit normal n
+ *     (pointing to increasing i on x-faces, increasing j on y-faces) and
+ *     area A = its length;
+ *   - cell gradient: central differences along the two mesh lines through
+ *     the centre, grad phi = J^-T (phi_i, phi_j) with J the Jacobian of the
+ *     centre positions along those lines (one-sided toward the inside at
+ *     the outer ghost layer of a non-periodic side);
+ *   - face value (linear), the uniform-mesh split of Sec 2.4 (normal slope
+ *     from the two cells, tangential slope from their gradients) carried
+ *     over: with d = x_R - x_L, the line between the centres crosses the
+ *     face at x_L + theta d, theta = ((x_b - x_L) . n) / (d . n), and
+ *     o = x_b - (x_L + theta d) lies along the face; phi_b = (1 - theta)
+ *     phi_L + theta phi_R + gbar . o with gbar = (1 - theta) grad phi_L +
+ *     theta grad phi_R; the face gradient g = gbar + ((phi_R - phi_L) -
+ *     gbar . d) n / (d . n) keeps gbar's tangential part and takes the
+ *     two-point difference along d; phi(x_b - h xi) = phi_b - h xi . g.
+ *     The upwind-cell value is phi_C + (x_b - h xi - x_C) . grad phi_C.  On
+ *     a tensor mesh both equal the tensor oracle's (o = 0, d along n);
+ *   - ghost cells: the first inner centre mirrored across the boundary face,
+ *     values by the side's rule with the wall extrapolation factor
+ *     e = ((x_g - x_1) . n) / ((x_1 - x_2) . n) (the ratio of the distances
+ *     to the wall); corners as on tensor meshes (x sides first, then y
+ *     sides over the padded width);
+ *   - boundary faces: the rules of Sec 2.5 with the face's own normal (the
+ *     symmetry rule needs a face normal along x or y, and mirrors across
+ *     that axis); segments by the face centre's y (W, E) or x (S, N);
+ *     periodic sides: the opposite side is a translate of it.
+ * Parity unpinned by the paper (the readings above are checked by the
+ * invariants of tests/test_oracle_pins.py and by reduction to the tensor
+ * oracle). */
+typedef struct {
+  int nx, ny;
+  const double *X, *Y; /* vertex coordinates [(ny+1)][(nx+1)] */
+  double RT, tau, dt;
+  int scheme, recon;
+  int nbc[4];
+  const orc_bc_segment *bc[4];
+} orc_quad_problem;
+
+/* Cell centres xc, yc and volumes vol, each [ny][nx] (any may be NULL). */
+int orc_quad_geometry(const orc_quad_problem *p, double *xc, double *yc, double *vol);
+/* The explicit step on the quad mesh, nsteps times, in place. */
+int orc_quad_step(const orc_quad_problem *p, double *f_tilde, long long nsteps);
+/* out[0] = sum rho |V|, out[1..2] = sum rho u |V| over the quad cells. */
+int orc_quad_conserved(const orc_quad_problem *p, const double *f_tilde, double *out);
+/* Eq. eq:cfl with dx the shortest face of the mesh. */
+int orc_quad_dt_from_cfl(const orc_quad_problem *p, double cfl, double *dt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -372,3 +372,68 @@ def cavity_at_ratio(point, ratio: float):
     case, fields = cavity(n, Re=Re, U=0.1, cfl=cfl, scheme=scheme)
     case["U"] = 0.1
     return case, fields
+
+
+# ---------------------------------------------------------------- quad meshes
+# Vertex arrays X, Y of shape [(ny+1), (nx+1)]; cell (i, j) has the vertices
+# (i, j), (i+1, j), (i+1, j+1), (i, j+1), counter-clockwise.
+
+def quad_from_faces(case):
+    """The tensor mesh of a case dict as vertex arrays (same problem)."""
+    X, Y = np.meshgrid(np.asarray(case["xf"], float), np.asarray(case["yf"], float))
+    out = {k: v for k, v in case.items() if k not in ("xf", "yf")}
+    out.update(X=X, Y=Y)
+    return out
+
+
+def quad_reindexed(case):
+    """The tensor mesh of a case dict with its index directions turned: quad
+    index i runs along +y, j along -x (vertex (i, j) at (xf[nx - j], yf[i])).
+    Sides map W->S, E->N, S->E, N->W of the tensor problem.  Returns the quad
+    case and the maps between [9, ny, nx] tensor arrays and quad arrays."""
+    xf, yf = np.asarray(case["xf"], float), np.asarray(case["yf"], float)
+    nx, ny = case["nx"], case["ny"]
+    jj, ii = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    X, Y = xf[nx - jj], yf[ii]
+    W_, E_, S_, N_ = case["bc"]
+    q = {k: v for k, v in case.items() if k not in ("xf", "yf")}
+    q.update(nx=ny, ny=nx, X=X, Y=Y, bc=[S_, N_, E_, W_])
+
+    def to_quad(a):   # tensor cell (i, j) -> quad cell (i' = j, j' = nx - 1 - i)
+        return np.ascontiguousarray(np.swapaxes(a, -1, -2)[..., ::-1, :])
+
+    def from_quad(a):
+        return np.ascontiguousarray(np.swapaxes(a[..., ::-1, :], -1, -2))
+    return q, to_quad, from_quad
+
+
+def quad_sheared(case, s: float):
+    """The tensor mesh of a case dict sheared along x: vertex (i, j) at
+    (xf[i] + s (yf[j] - yf[0]), yf[j])."""
+    q = quad_from_faces(case)
+    q["X"] = q["X"] + s * (q["Y"] - q["Y"][0, 0])
+    return q
+
+
+def quad_wavy_periodic(n: int, L: float = 2 * math.pi, amp: float = 0.05):
+    """Doubly periodic n x n mesh of [0, L)^2 with smooth sinusoidal
+    distortion of the mesh lines (vertices x = a + A L sin(2 pi a / L)
+    sin(2 pi b / L), y = b + A L sin(2 pi a / L) sin(2 pi b / L)); the sides
+    stay straight and translates of one another."""
+    a = np.linspace(0.0, L, n + 1)
+    A, B = np.meshgrid(a, a)
+    d = amp * L * np.sin(2 * math.pi * A / L) * np.sin(2 * math.pi * B / L)
+    return A + d, B + d
+
+
+def quad_random_interior(nx: int, ny: int, seed: int, amp: float = 0.2, L=(1.0, 1.0)):
+    """A rectangle [0, Lx] x [0, Ly] with interior vertices moved at random by
+    up to amp of a cell (boundary vertices slide along their side only)."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.linspace(0.0, L[0], nx + 1), np.linspace(0.0, L[1], ny + 1))
+    dx, dy = L[0] / nx, L[1] / ny
+    X[1:-1, 1:-1] += amp * dx * rng.uniform(-1, 1, (ny - 1, nx - 1))
+    Y[1:-1, 1:-1] += amp * dy * rng.uniform(-1, 1, (ny - 1, nx - 1))
+    X[[0, -1], 1:-1] += amp * dx * rng.uniform(-1, 1, (2, nx - 1))
+    Y[1:-1, [0, -1]] += amp * dy * rng.uniform(-1, 1, (ny - 1, 2))
+    return X, Y
