@@ -562,6 +562,25 @@ static void face_to_f(const vset *v, const orc_problem *p, double *val) {
 /* The explicit step                                                  */
 /* ------------------------------------------------------------------ */
 
+/* Sec 2.2 cell stage of one direction: f_tilde^+ and the value phi the
+ * faces reconstruct (f_bar^+ for DUGKS, f_tilde^+ for BKG, the cell f^n for
+ * the collision-free faces of Eqs. cfd1 / cfd2). */
+static void cell_stage(int scheme, double tau, double dt, double f, double fe, double *tplus,
+                       double *phi) {
+  const double h = 0.5 * dt;
+  *tplus = ((2.0 * tau - dt) * f + 2.0 * dt * fe) / (2.0 * tau + dt);
+  if (scheme == ORC_DUGKS)
+    *phi = ((2.0 * tau - h) * f + 3.0 * h * fe) / (2.0 * tau + dt);
+  else if (scheme == ORC_BKG)
+    *phi = *tplus;
+  else /* collision-free faces: the cell f^n itself */
+    *phi = (2.0 * tau * f + dt * fe) / (2.0 * tau + dt);
+}
+
+/* Distance h the face value is taken back along the characteristic; the
+ * central collision-free face takes phi at x_b itself. */
+static double face_shift(int scheme, double h) { return scheme == ORC_CFREE_CENTRAL ? 0.0 : h; }
+
 static int step_once(const orc_problem *p, const vset *v, const geom *g, double *ft,
                      double *P, double *TP, double *FX, double *FY) {
   const int nx = g->nx, ny = g->ny;
@@ -577,14 +596,8 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
       moments_of(v, f9, &rho, &ux, &uy);
       feq_of(v, rho, ux, uy, fe);
       for (int a = 0; a < 9; ++a) {
-        double tplus = ((2.0 * tau - dt) * f9[a] + 2.0 * dt * fe[a]) / (2.0 * tau + dt);
-        double phi;
-        if (p->scheme == ORC_DUGKS)
-          phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);
-        else if (p->scheme == ORC_BKG)
-          phi = tplus;
-        else /* collision-free faces: the cell f^n itself */
-          phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);
+        double tplus, phi;
+        cell_stage(p->scheme, tau, dt, f9[a], fe[a], &tplus, &phi);
         TP[a * n + k] = tplus;
         P[a * plane + PIDX(g, i, j)] = phi;
       }
@@ -595,7 +608,7 @@ static int step_once(const orc_problem *p, const vset *v, const geom *g, double 
 
   /* 4-6: x-faces i = 0..nx, rows 0..ny-1; the central collision-free face
      takes phi at x_b itself (no shift along the characteristic) */
-  const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;
+  const double hs = face_shift(p->scheme, h);
   for (int j = 0; j < ny; ++j) {
     for (int i = 0; i <= nx; ++i) {
       recon_xface(v, g, P, i, j, hs, p->recon, val);
@@ -1336,20 +1349,14 @@ static int qstep_once(const orc_quad_problem *p, const vset *v, const qgeom *g, 
       moments_of(v, f9, &rho, &ux, &uy);
       feq_of(v, rho, ux, uy, fe);
       for (int a = 0; a < 9; ++a) {
-        const double tplus = ((2.0 * tau - dt) * f9[a] + 2.0 * dt * fe[a]) / (2.0 * tau + dt);
-        double phi;
-        if (p->scheme == ORC_DUGKS)
-          phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);
-        else if (p->scheme == ORC_BKG)
-          phi = tplus;
-        else
-          phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);
+        double tplus, phi;
+        cell_stage(p->scheme, tau, dt, f9[a], fe[a], &tplus, &phi);
         TP[a * n + k] = tplus;
         P[a * plane + QIDX(g, i, j)] = phi;
       }
     }
   qfill_ghosts(v, g, P);
-  const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;
+  const double hs = face_shift(p->scheme, h);
   for (int j = 0; j < ny; ++j)
     for (int k = 0; k <= nx; ++k) {
       const size_t f = (size_t)j * (nx + 1) + k;

@@ -623,8 +623,8 @@ MUTATIONS = {
     "flux_sign": ("ft[a * n + k] = TP[a * n + k] - dt / vol * out_flux;",
                   "ft[a * n + k] = TP[a * n + k] + dt / vol * out_flux;"),
     # f_bar^+ coefficient with dt in place of h
-    "fbar_coef": ("phi = ((2.0 * tau - h) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);",
-                  "phi = ((2.0 * tau - dt) * f9[a] + 3.0 * h * fe[a]) / (2.0 * tau + dt);"),
+    "fbar_coef": ("*phi = ((2.0 * tau - h) * f + 3.0 * h * fe) / (2.0 * tau + dt);",
+                  "*phi = ((2.0 * tau - dt) * f + 3.0 * h * fe) / (2.0 * tau + dt);"),
     # back-transform at the face uses dt = 2h instead of h
     "face_back": ("val[a] = (2.0 * tau * val[a] + h * fe[a]) / (2.0 * tau + h);",
                   "val[a] = (2.0 * tau * val[a] + 2.0 * h * fe[a]) / (2.0 * tau + 2.0 * h);"),
@@ -632,11 +632,9 @@ MUTATIONS = {
     "bounce_sign": ("val[v->opp[a]] = orig[a] - 2.0 * v->w[a] * xu / v->cs2;",
                     "val[v->opp[a]] = orig[a] + 2.0 * v->w[a] * xu / v->cs2;"),
     # the central collision-free face taken at the foot of the characteristic
-    "central_shift": ("const double hs = p->scheme == ORC_CFREE_CENTRAL ? 0.0 : h;",
-                      "const double hs = h;"),
+    "central_shift": ("return scheme == ORC_CFREE_CENTRAL ? 0.0 : h;", "return h;"),
     # the collision-free faces reconstructing f_tilde^+ instead of f^n
-    "cfree_phi": ("phi = (2.0 * tau * f9[a] + dt * fe[a]) / (2.0 * tau + dt);",
-                  "phi = tplus;"),
+    "cfree_phi": ("*phi = (2.0 * tau * f + dt * fe) / (2.0 * tau + dt);", "*phi = *tplus;"),
     # the set-density outflow moving the ghost's density the wrong way
     "outflow_neq_sign": ("for (int a = 0; a < 9; ++a) pg[a] = p1[a] + (es[a] - e1[a]);",
                          "for (int a = 0; a < 9; ++a) pg[a] = p1[a] - (es[a] - e1[a]);"),
