@@ -289,9 +289,9 @@ def accuracy(dv, scheme, precision, sizes=(256,), target_n=4096):
     return out
 
 
-def case_throughput(dv, stream, torch, case, fields, precision, steps, peak):
+def case_throughput(dv, stream, torch, case, fields, precision, steps, peak, path="fused"):
     """MLUPS and HBM fraction of one workload (autotuned launch shape)."""
-    s = dv.Solver(case, precision=precision, stream=stream.cuda_stream)
+    s = dv.Solver(case, precision=precision, stream=stream.cuda_stream, path=path)
     try:
         s.init_equilibrium(*fields)
         s.autotune(10)
@@ -517,6 +517,16 @@ def main():
             extras[f"plate_512x256_{scheme}_f32_dev"] = dict(case_throughput(
                 dv, stream, torch, c4, fl4, "f32_dev", 400, peak),
                 note="4.7 MB buffers, resident in L2: not HBM-bound")
+        # curvilinear meshes: the multi-pass FP64 step on a wavy 1024^2 mesh,
+        # beside the same step on the uniform tensor mesh and the fused FP64 step
+        cq, flq = W.taylor_green_quad(1024, scheme="dugks")
+        extras["quad_wavy_1024_dugks_f64_multipass"] = dict(case_throughput(
+            dv, stream, torch, cq, flq, "f64", 40, peak),
+            note="six kernels per step with face arrays; hbm_frac against the 144 B/cell minimum")
+        ct, flt = workload(1024, "dugks")
+        extras["tensor_1024_dugks_f64_multipass"] = case_throughput(
+            dv, stream, torch, ct, flt, "f64", 40, peak, path="multipass")
+        extras["tensor_1024_dugks_f64_fused"] = case_throughput(dv, stream, torch, ct, flt, "f64", 40, peak)
         extras["batched_vs_per_case_loop"] = batched_vs_loop(dv, torch, steps=a.batch_steps)
     s.close()
     sizes = tuple(int(x) for x in a.accuracy_sizes.split(",") if x)

@@ -155,8 +155,45 @@ DVBE_API dvbe_status dvbe_d2q9(double RT, double *xi, double *w, int *opp);
 DVBE_API dvbe_status dvbe_mesh_create(int nx, int ny, const double *xf, const double *yf,
                              dvbe_mesh *out);
 DVBE_API void dvbe_mesh_destroy(dvbe_mesh mesh);
-/* Cell centres xc[nx], yc[ny] and volumes |V_k| vol[ny][nx] (any may be NULL). */
+/* Cell centres xc[nx], yc[ny] and volumes |V_k| vol[ny][nx] (any may be NULL)
+ * of a tensor mesh; DVBE_ERR_UNSUPPORTED for a quadrilateral mesh. */
 DVBE_API dvbe_status dvbe_mesh_geometry(dvbe_mesh mesh, double *xc, double *yc, double *vol);
+
+/* Curvilinear structured mesh of general quadrilateral cells (the FV form of
+ * Sec 2.2 holds for cells V_k with faces of any orientation).  X, Y are the
+ * vertex coordinates [(ny+1)][(nx+1)], row-major, copied; cell (i, j) has the
+ * vertices (i, j), (i+1, j), (i+1, j+1), (i, j+1), counter-clockwise.  Every
+ * cell's area must be positive (else DVBE_ERR_INVALID_ARG); nx, ny >= 2.
+ * On this mesh:
+ *   - cell centre = mean of the four vertices, volume = area; face = the
+ *     edge between two cells, with its midpoint x_b, unit normal n (towards
+ *     increasing i on x-faces, increasing j on y-faces) and length A;
+ *   - the face value phi(x_b - h xi) generalises the linear reconstruction
+ *     of Sec 2.4: the line between the centres x_L, x_R crosses the face at
+ *     x_L + theta d (d = x_R - x_L, theta = ((x_b - x_L) . n) / (d . n)),
+ *     phi_b = (1 - theta) phi_L + theta phi_R + gbar . (x_b - x_L - theta d)
+ *     with gbar the theta-blend of the two cells' gradients, and the face
+ *     gradient g = gbar + ((phi_R - phi_L) - gbar . d) n / (d . n), so that
+ *     phi(x_b - h xi) = phi_b - h xi . g.  Cell gradients: central
+ *     differences along the two mesh lines, mapped by the inverse Jacobian of
+ *     the centre positions (one-sided at the outer ghost layer of a side that
+ *     is not periodic).  DVBE_RECON_UPWIND_CELL: phi_C + (x_b - h xi - x_C) .
+ *     grad phi_C;
+ *   - ghost centres: the first inner centre mirrored across the boundary
+ *     face; wall extrapolation factor e = ((x_g - x_1) . n) / ((x_1 - x_2) .
+ *     n); the rules of Sec 2.5 with the face's own normal; symmetry sides
+ *     need faces normal to x or y; boundary segments are chosen by the face
+ *     midpoint's y (W, E) or x (S, N); a periodic pair of sides must be
+ *     translates of each other.
+ * A tensor mesh given this way steps as dvbe_mesh_create's up to rounding.
+ * Solvers on a quadrilateral mesh run the multi-pass FP64 step
+ * (DVBE_PATH_MULTIPASS, DVBE_F64; otherwise DVBE_ERR_UNSUPPORTED); batches
+ * take tensor meshes only. */
+DVBE_API dvbe_status dvbe_mesh_create_quad(int nx, int ny, const double *X, const double *Y,
+                                           dvbe_mesh *out);
+/* Cell centres and volumes of either kind of mesh, each [ny][nx] (any may be
+ * NULL). */
+DVBE_API dvbe_status dvbe_mesh_cells(dvbe_mesh mesh, double *xc, double *yc, double *vol);
 /* n+1 faces: uniform on [a, b]; tanh-clustered toward both ends,
  * a + (b-a)(1 + tanh(beta(2s-1))/tanh(beta))/2 with s = i/n; geometric from a
  * with first width d0 and growth ratio. */
@@ -164,7 +201,8 @@ DVBE_API dvbe_status dvbe_faces_uniform(int n, double a, double b, double *out);
 DVBE_API dvbe_status dvbe_faces_tanh(int n, double a, double b, double beta, double *out);
 DVBE_API dvbe_status dvbe_faces_geometric(int n, double a, double d0, double ratio, double *out);
 /* Eq. eq:cfl: dt = cfl * dx_min / (sqrt(6) c_s), dx_min the smallest cell
- * width of the mesh in either direction. */
+ * width of the mesh in either direction (on a quadrilateral mesh, the
+ * shortest cell edge). */
 DVBE_API dvbe_status dvbe_dt_from_cfl(dvbe_mesh mesh, double RT, double cfl, double *dt);
 
 /* ---- device memory ------------------------------------------------------ */
@@ -244,7 +282,9 @@ DVBE_API dvbe_status dvbe_set_launch(dvbe_solver s, const dvbe_launch *in);
  * each with a grid of one block per strip group or one wave of blocks.  The
  * choice is cached (dvbe_set_autotune_cache) under the scheme, precision,
  * mesh size and periodicity, GPU model and library build: a later call with
- * the same key takes the cached shape without timing anything. */
+ * the same key takes the cached shape without timing anything.  A solver on
+ * the multi-pass path has no launch shape: the call returns at once with
+ * best_ms = 0. */
 DVBE_API dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms);
 /* Autotuner cache file (JSON).  NULL: no cache; "": the default, which is
  * $DVBE_AUTOTUNE_CACHE if set (empty: no cache), else

@@ -73,6 +73,8 @@ _lib = None
 _SIGS = {
     "dvbe_d2q9": [ctypes.c_double, _DP, _DP, ctypes.POINTER(ctypes.c_int)],
     "dvbe_mesh_create": [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.POINTER(ctypes.c_void_p)],
+    "dvbe_mesh_create_quad": [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.POINTER(ctypes.c_void_p)],
+    "dvbe_mesh_cells": [ctypes.c_void_p, _DP, _DP, _DP],
     "dvbe_mesh_destroy": [ctypes.c_void_p],
     "dvbe_mesh_geometry": [ctypes.c_void_p, _DP, _DP, _DP],
     "dvbe_faces_uniform": [ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP],
@@ -218,6 +220,30 @@ def dvbe_mesh_create(xf, yf):
     return h
 
 
+def dvbe_mesh_create_quad(X, Y):
+    """Quadrilateral mesh from vertex arrays X, Y of shape [ny+1, nx+1]."""
+    X, Y = _f64(X), _f64(Y)
+    if X.ndim != 2 or X.shape != Y.shape:
+        raise ValueError("X and Y must be 2-D arrays of one shape [ny+1, nx+1]")
+    h = ctypes.c_void_p()
+    _call("dvbe_mesh_create_quad", X.shape[1] - 1, X.shape[0] - 1, _dp(X), _dp(Y), ctypes.byref(h))
+    return h
+
+
+def dvbe_mesh_cells(mesh, nx, ny):
+    xc, yc, vol = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
+    _call("dvbe_mesh_cells", mesh, _dp(xc), _dp(yc), _dp(vol))
+    return xc, yc, vol
+
+
+def mesh_of(case: dict):
+    """The library mesh of a case dict: vertex arrays X, Y (quadrilateral
+    cells) or face coordinates xf, yf (tensor mesh)."""
+    if "X" in case:
+        return dvbe_mesh_create_quad(case["X"], case["Y"])
+    return dvbe_mesh_create(case["xf"], case["yf"])
+
+
 def dvbe_mesh_destroy(mesh):
     lib().dvbe_mesh_destroy(mesh)
 
@@ -339,7 +365,9 @@ def use_torch_allocator(enable: bool = True):
 class Solver:
     """One problem on the GPU: create, init, step, read back (dvbe_solver_*).
 
-    case: dict with nx, ny, xf[nx+1], yf[ny+1] (face coordinates), RT, tau,
+    case: dict with nx, ny, and either xf[nx+1], yf[ny+1] (face coordinates of
+    a tensor mesh) or X, Y [ny+1][nx+1] (vertices of quadrilateral cells,
+    which run the multi-pass FP64 step), RT, tau,
     dt, scheme ("dugks", "bkg", "cfree_upwind", "cfree_central"), optionally
     recon ("linear" or "upwind_cell", the latter on the multi-pass path), and bc, four
     lists (W, E, S, N) of segments (kind, s0, s1, rho, ux, uy) with kind one
@@ -356,7 +384,7 @@ class Solver:
         self.case = case
         self.nx, self.ny = int(case["nx"]), int(case["ny"])
         self.precision = precision
-        mesh = dvbe_mesh_create(case["xf"], case["yf"])
+        mesh = mesh_of(case)
         try:
             params, keep = make_params(case, mesh, precision, stream, allow_cfl_ge_1, bkg_fd,
                                        dev_scale, rho0, path)
@@ -516,7 +544,7 @@ class Batch:
         arr = (dvbe_params * len(cases))()
         try:
             for k, case in enumerate(cases):
-                m = dvbe_mesh_create(case["xf"], case["yf"])
+                m = mesh_of(case)
                 meshes.append(m)
                 p, keep = make_params(case, m, precision, allow_cfl_ge_1=allow_cfl_ge_1)
                 keeps.append(keep)

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdvbe.so")
 SOURCES = ["step_f64.cu", "step_f32.cu", "step_f16.cu", "aux_kernels.cu", "dvbe_capi.cu", "batch.cu",
-           "noalloc.cu", "tune_cache.cu", "multipass.cu"]
+           "noalloc.cu", "tune_cache.cu", "multipass.cu", "quad_mesh.cu"]
 HEADERS = ["internal.h", "capi_common.h", "step_kernel.cuh"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -210,7 +210,8 @@ __device__ __forceinline__ void block_reduce3(double s0, double s1, double s2, d
   }
 }
 
-__global__ void k_conserved(FieldView v, const double *volx, const double *voly, double *partials) {
+__global__ void k_conserved(FieldView v, const double *volx, const double *voly, const double *volc,
+                            long long vpitch, double *partials) {
   const long long n = (long long)v.nx * v.ny;
   double m = 0, jx = 0, jy = 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -218,7 +219,7 @@ __global__ void k_conserved(FieldView v, const double *volx, const double *voly,
     const int j = (int)(k / v.nx), i = (int)(k % v.nx);
     double r, u, w;
     cell_moments(v, k, r, u, w);
-    const double vol = volx[i] * voly[j];
+    const double vol = volc ? volc[(long long)j * vpitch + i] : volx[i] * voly[j];
     m += r * vol;
     jx += r * u * vol;
     jy += r * w * vol;
@@ -323,8 +324,9 @@ cudaError_t aux_moments(const FieldView &v, double *r, double *u, double *w, cud
 }
 
 cudaError_t aux_conserved(const FieldView &v, const double *volx, const double *voly,
-                          double *partials, double *out, cudaStream_t s) {
-  k_conserved<<<kReduceBlocks, kRT, 0, s>>>(v, volx, voly, partials);
+                          const double *volc, long long vpitch, double *partials, double *out,
+                          cudaStream_t s) {
+  k_conserved<<<kReduceBlocks, kRT, 0, s>>>(v, volx, voly, volc, vpitch, partials);
   k_finish3<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
   return cudaGetLastError();
 }

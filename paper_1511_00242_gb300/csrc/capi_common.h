@@ -8,10 +8,43 @@
 
 struct dvbe_mesh_ {
   int nx, ny;
-  std::vector<double> xf, yf;
+  std::vector<double> xf, yf;   // tensor mesh: face coordinates
+  bool quad = false;            // quadrilateral mesh: vertex coordinates
+  std::vector<double> X, Y;     // [(ny+1)][(nx+1)]
 };
 
 namespace dvbe {
+
+// Face tables of a quadrilateral mesh, one array of each per face (x-faces
+// [ny][nx+1], y-faces [ny+1][nx]); lengths scaled by s = h c (1 for the
+// central face).  L, R: the cells on either side (R on the normal's side).
+enum {
+  QF_TH,      // theta: the centre line crosses the face at x_L + theta d
+  QF_OX,      // (x_b - x_L - theta d) / s
+  QF_OY,
+  QF_DX,      // d / s = (x_R - x_L) / s
+  QF_DY,
+  QF_TX,      // n s / (d . n): face-gradient correction direction
+  QF_TY,
+  QF_BX,      // (x_b - x_L) / s
+  QF_BY,
+  QF_NX,      // unit normal n
+  QF_NY,
+  QF_AX,      // n A: the flux weight of the update
+  QF_AY,
+  kQF
+};
+
+// Geometry of a quadrilateral mesh for the multi-pass step (quad_mesh.cu).
+struct QuadHost {
+  std::vector<double> jinv;     // [4][(nx+4)(ny+4)]: s J^-T of the padded cells
+  std::vector<double> fx, fy;   // [kQF][faces]
+  std::vector<double> vs, vol;  // [ny][nx]: dt c / |V|, |V|
+  std::vector<double> ext;      // wall extrapolation: W, E [ny] each, then S, N [nx+4] each
+  std::vector<unsigned char> mir; // as ext: 1 when the face normal lies along x
+  std::vector<double> bn;       // outward normals (x, y): W, E [2 ny] each, then S, N [2 nx] each
+  double s = 1, eshift = 1;     // length scale of the tables; 0: the central face
+};
 
 // A validated problem with its host geometry tables (double precision).
 struct Problem {
@@ -30,6 +63,8 @@ struct Problem {
   int recon = 0;               // dvbe_recon
   bool multipass = false;      // multi-pass FP64 step with face arrays
   std::vector<double> xg, yg, xoff, yoff; // its gradient and foot-offset tables (MPArgs)
+  bool quad = false;           // quadrilateral mesh (multi-pass step only)
+  QuadHost q;
   int pitch = 0, elem = 0;
   long long plane = 0;
 };
@@ -52,7 +87,16 @@ struct MPArgs {
   const double *yoff;  // [2(ny+1)]
   double b_tp;         // f_tilde^+ = f_tilde + b_tp (f_eq - f_tilde)
   int nx, ny, recon, scheme;
+  // quadrilateral mesh (QuadHost on the device); quad == 0 on tensor meshes
+  int quad;
+  double eshift;
+  const double *jinv, *qfx, *qfy, *vs, *qext, *qbn;
+  const unsigned char *qmir;
 };
+// Tables of a quadrilateral mesh: validates it against the boundary
+// segments and fills pb.q, pb.segid and the CFL number.
+dvbe_status quad_tables(const dvbe_mesh_ &m, Problem &pb);
+double quad_min_edge(const dvbe_mesh_ &m); // shortest cell edge
 cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s);
 constexpr int kMultipassKernels = 6; // launches of one multi-pass step
 

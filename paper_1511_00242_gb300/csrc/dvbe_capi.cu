@@ -132,6 +132,7 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   pb.ny = m.ny;
   pb.xf = m.xf;
   pb.yf = m.yf;
+  pb.quad = m.quad;
   pb.RT = p->RT;
   pb.tau = p->tau;
   pb.dt = p->dt;
@@ -163,8 +164,12 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
 
   // Eq. eq:cfl
   double dmin = INFINITY;
-  for (int i = 0; i < pb.nx; ++i) dmin = std::min(dmin, pb.xf[i + 1] - pb.xf[i]);
-  for (int j = 0; j < pb.ny; ++j) dmin = std::min(dmin, pb.yf[j + 1] - pb.yf[j]);
+  if (m.quad) {
+    dmin = quad_min_edge(m);
+  } else {
+    for (int i = 0; i < pb.nx; ++i) dmin = std::min(dmin, pb.xf[i + 1] - pb.xf[i]);
+    for (int j = 0; j < pb.ny; ++j) dmin = std::min(dmin, pb.yf[j + 1] - pb.yf[j]);
+  }
   pb.cfl = pb.dt * std::sqrt(6.0 * pb.RT) / dmin;
   if (pb.cfl >= 1.0 && !p->allow_cfl_ge_1) {
     char b[160];
@@ -178,7 +183,10 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   if (p->path != DVBE_PATH_FUSED && p->path != DVBE_PATH_MULTIPASS)
     return fail(DVBE_ERR_INVALID_ARG, "unknown step path");
   pb.recon = p->recon;
-  pb.multipass = p->path == DVBE_PATH_MULTIPASS || p->recon == DVBE_RECON_UPWIND_CELL;
+  pb.multipass = p->path == DVBE_PATH_MULTIPASS || p->recon == DVBE_RECON_UPWIND_CELL || m.quad;
+  if (m.quad && (p->precision != DVBE_F64 || p->bkg_fd))
+    return fail(DVBE_ERR_UNSUPPORTED, "a quadrilateral mesh runs the multi-pass step, in FP64 "
+                                      "and finite-volume form only");
   if (pb.multipass && (p->precision != DVBE_F64 || p->bkg_fd))
     return fail(DVBE_ERR_UNSUPPORTED, "the multi-pass step (and the upwind-cell reconstruction) runs "
                                       "in FP64 and finite-volume form only");
@@ -256,7 +264,7 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
     const bool xs = s < 2;
     const int n = xs ? ny : nx;
     pb.segid[s].assign(n, 0);
-    if (per[s]) continue;
+    if (per[s] || m.quad) continue; // quadrilateral meshes: by face midpoint (quad_tables)
     for (int k = 0; k < n; ++k) {
       const double t = xs ? ycb[k + 1] : xcb[k + 1];
       int g = find_seg(pb.bc[s], t);
@@ -282,6 +290,10 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
     pb.b_phi = 2 * dt / (2 * tau + dt); // f_tilde^+ = ((2 tau - dt) f_tilde + 2 dt f_eq) / (2 tau + dt)
   pb.q_face = h / (2 * tau + h);        // f = (2 tau f_bar + h f_eq) / (2 tau + h)
   pb.b_tp = 2 * dt / (2 * tau + dt);    // f_tilde^+ of every scheme
+  if (m.quad) {
+    dvbe_status st = quad_tables(m, pb);
+    if (st != DVBE_OK) return st;
+  }
   if (pb.multipass) {
     // cell centres c = -2 .. n+1 (periodic: shifted images; otherwise the
     // mirror ghost at -1 and n, unused beyond), the central-difference factor
@@ -561,6 +573,7 @@ struct dvbe_solver_ {
   StepStreams ss{}; // main = stream; side stream and fork / join events of the two-kernel step
   MPArgs mp{};      // multi-pass step: buffers and tables (one allocation), when used
   char *mpblob = nullptr;
+  const double *qvol = nullptr; // cell volumes of a quadrilateral mesh (in mpblob)
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned *flag = nullptr;
@@ -579,20 +592,30 @@ static dvbe_status alloc_multipass(dvbe_solver s) {
   const Problem &pb = s->pb;
   const long long nx = pb.nx, ny = pb.ny;
   const long long pplane = (nx + 4) * (ny + 4);
-  const long long counts[8] = {9 * pplane, 9 * nx * ny, 9 * (nx + 1) * ny, 9 * nx * (ny + 1),
-                               nx + 4, ny + 4, 2 * (nx + 1), 2 * (ny + 1)};
-  size_t off[8], total = 0;
-  for (int q = 0; q < 8; ++q) {
+  // buffers, the tensor tables, then the quadrilateral-mesh tables (empty
+  // on tensor meshes); the mirror flags (bytes) last
+  const QuadHost &qh = pb.q;
+  const std::vector<double> *tab[11] = {&pb.xg, &pb.yg, &pb.xoff, &pb.yoff, &qh.jinv, &qh.fx,
+                                        &qh.fy, &qh.vs, &qh.vol, &qh.ext, &qh.bn};
+  long long counts[16] = {9 * pplane, 9 * nx * ny, 9 * (nx + 1) * ny, 9 * nx * (ny + 1)};
+  for (int q = 0; q < 11; ++q) counts[4 + q] = (long long)tab[q]->size();
+  size_t off[16], total = 0;
+  for (int q = 0; q < 15; ++q) {
     off[q] = total;
     total += ((size_t)counts[q] * sizeof(double) + 255) / 256 * 256;
   }
+  off[15] = total;
+  total += (qh.mir.size() + 255) / 256 * 256;
   s->mpblob = (char *)dmalloc(total, s->stream);
   if (!s->mpblob) return fail(DVBE_ERR_OOM, "device allocation of the multi-pass buffers failed");
-  const std::vector<double> *tab[4] = {&pb.xg, &pb.yg, &pb.xoff, &pb.yoff};
   cudaError_t e = cudaMemsetAsync(s->mpblob, 0, total, s->stream);
-  for (int q = 0; q < 4 && e == cudaSuccess; ++q)
-    e = cudaMemcpyAsync(s->mpblob + off[4 + q], tab[q]->data(), sizeof(double) * tab[q]->size(),
-                        cudaMemcpyHostToDevice, s->stream);
+  for (int q = 0; q < 11 && e == cudaSuccess; ++q)
+    if (!tab[q]->empty())
+      e = cudaMemcpyAsync(s->mpblob + off[4 + q], tab[q]->data(), sizeof(double) * tab[q]->size(),
+                          cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && !qh.mir.empty())
+    e = cudaMemcpyAsync(s->mpblob + off[15], qh.mir.data(), qh.mir.size(), cudaMemcpyHostToDevice,
+                        s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "multi-pass set-up");
   MPArgs &m = s->mp;
@@ -610,6 +633,16 @@ static dvbe_status alloc_multipass(dvbe_solver s) {
   m.ny = pb.ny;
   m.recon = pb.recon;
   m.scheme = pb.kernel;
+  m.quad = pb.quad ? 1 : 0;
+  m.eshift = qh.eshift;
+  m.jinv = (const double *)(s->mpblob + off[8]);
+  m.qfx = (const double *)(s->mpblob + off[9]);
+  m.qfy = (const double *)(s->mpblob + off[10]);
+  m.vs = (const double *)(s->mpblob + off[11]);
+  s->qvol = (const double *)(s->mpblob + off[12]);
+  m.qext = (const double *)(s->mpblob + off[13]);
+  m.qbn = (const double *)(s->mpblob + off[14]);
+  m.qmir = (const unsigned char *)(s->mpblob + off[15]);
   return DVBE_OK;
 }
 
@@ -679,6 +712,8 @@ void dvbe_mesh_destroy(dvbe_mesh mesh) { delete mesh; }
 
 dvbe_status dvbe_mesh_geometry(dvbe_mesh m, double *xc, double *yc, double *vol) {
   if (!m) return fail(DVBE_ERR_INVALID_ARG, "NULL mesh");
+  if (m->quad)
+    return fail(DVBE_ERR_UNSUPPORTED, "a quadrilateral mesh has no face coordinates: use dvbe_mesh_cells");
   for (int i = 0; i < m->nx && xc; ++i) xc[i] = 0.5 * (m->xf[i] + m->xf[i + 1]);
   for (int j = 0; j < m->ny && yc; ++j) yc[j] = 0.5 * (m->yf[j] + m->yf[j + 1]);
   if (vol)
@@ -714,8 +749,12 @@ dvbe_status dvbe_faces_geometric(int n, double a, double d0, double ratio, doubl
 dvbe_status dvbe_dt_from_cfl(dvbe_mesh m, double RT, double cfl, double *dt) {
   if (!m || !(RT > 0) || !(cfl > 0) || !dt) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
   double dmin = INFINITY;
-  for (int i = 0; i < m->nx; ++i) dmin = std::min(dmin, m->xf[i + 1] - m->xf[i]);
-  for (int j = 0; j < m->ny; ++j) dmin = std::min(dmin, m->yf[j + 1] - m->yf[j]);
+  if (m->quad) {
+    dmin = quad_min_edge(*m);
+  } else {
+    for (int i = 0; i < m->nx; ++i) dmin = std::min(dmin, m->xf[i + 1] - m->xf[i]);
+    for (int j = 0; j < m->ny; ++j) dmin = std::min(dmin, m->yf[j + 1] - m->yf[j]);
+  }
   *dt = cfl * dmin / (std::sqrt(6.0) * std::sqrt(RT));
   return DVBE_OK;
 }
@@ -993,7 +1032,8 @@ dvbe_status dvbe_get_moments(dvbe_solver s, double *rho, double *ux, double *uy)
 dvbe_status dvbe_conserved(dvbe_solver s, double out[3]) {
   if (!s || !out) return fail(DVBE_ERR_INVALID_ARG, "NULL argument");
   double *res = s->red + kReduceBlocks * 3;
-  cudaError_t e = aux_conserved(cur_view(s), s->dp.volx, s->dp.voly, s->red, res, s->stream);
+  cudaError_t e = aux_conserved(cur_view(s), s->dp.volx, s->dp.voly, s->qvol, s->pb.nx, s->red, res,
+                                s->stream);
   s->launches += 2;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -1103,6 +1143,10 @@ static void apply_launch(dvbe_solver s, const dvbe_launch &l) {
 
 dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
   if (!s || steps < 1) return fail(DVBE_ERR_INVALID_ARG, "bad argument");
+  if (s->pb.multipass) { // its kernels take no launch shape
+    if (best_ms) *best_ms = 0.0;
+    return DVBE_OK;
+  }
   const dvbe_launch saved = s->launch;
   const std::string key = solver_tune_key(s);
   TuneEntry hit;
@@ -1232,7 +1276,9 @@ dvbe_status dvbe_conserved_window(dvbe_solver s, int i0, int j0, int nx, int ny,
   v.nx = nx;
   v.ny = ny;
   double *res = s->red + kReduceBlocks * 3;
-  cudaError_t e = aux_conserved(v, s->dp.volx + i0, s->dp.voly + j0, s->red, res, s->stream);
+  cudaError_t e = aux_conserved(v, s->dp.volx + i0, s->dp.voly + j0,
+                                s->qvol ? s->qvol + (long long)j0 * s->pb.nx + i0 : nullptr, s->pb.nx,
+                                s->red, res, s->stream);
   s->launches += 2;
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

@@ -141,8 +141,11 @@ cudaError_t aux_moments(const FieldView &v, double *d_rho, double *d_ux, double 
 // Deterministic FP64 reductions; partials must hold kReduceBlocks * 3 doubles,
 // result 3 doubles.
 constexpr int kReduceBlocks = 296;
+// Cell volumes: d_vol_c[j * vpitch + i] when d_vol_c is not NULL (a
+// quadrilateral mesh), else d_vol_x[i] * d_vol_y[j].
 cudaError_t aux_conserved(const FieldView &v, const double *d_vol_x, const double *d_vol_y,
-                          double *d_partials, double *d_out, cudaStream_t s);
+                          const double *d_vol_c, long long vpitch, double *d_partials, double *d_out,
+                          cudaStream_t s);
 // One line of cells (axis 0: a column over rows lo..lo+n-1, axis 1: a row
 // over columns lo..lo+n-1) of all nine fields to / from a dense buffer
 // [9][n] of elem-byte elements, as stored.

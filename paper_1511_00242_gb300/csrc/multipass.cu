@@ -18,6 +18,8 @@
 //
 // Everything is FP64 on f_tilde itself; the geometry tables are those of
 // the fused kernel (CaseArgs) plus the foot offsets of the upwind cells.
+// Quadrilateral meshes run the same stages with their own ghost, face and
+// update kernels (tables of quad_mesh.cu).
 #include "capi_common.h"
 #include "step_kernel.cuh"
 
@@ -229,6 +231,217 @@ __global__ void k_update(CaseArgs A, MPArgs m) {
   }
 }
 
+// ---- quadrilateral meshes -------------------------------------------------
+//
+// Tables (QuadHost, lengths over s = h c): per padded cell s J^-T, per face
+// theta, the offset o of the face midpoint from the centre line, d = x_R -
+// x_L, the correction direction n s / (d . n), x_b - x_L, the unit normal n
+// and n A.  The face value is
+//   linear:      phi_b - e . g,  phi_b = (1 - theta) phi_L + theta phi_R + gbar . o,
+//                g = gbar + ((phi_R - phi_L) - gbar . d) n s / (d . n)
+//   upwind cell: phi_C + ((x_b - x_C) / s - e) . grad_C
+// with gbar the theta-blend of the cells' gradients (all scaled by s) and
+// e = xi / c; the central collision-free face drops the e . g term.
+
+// s grad phi at padded cell (i, j): central differences along the mesh
+// lines, one-sided at the outer ghost layer of a side that is not periodic.
+__device__ __forceinline__ void qgrad(const CaseArgs &A, const MPArgs &m, const double *Pa, int i,
+                                      int j, double &gx, double &gy) {
+  const int im = (!A.per_x && i <= -1) ? i : i - 1, ip = (!A.per_x && i >= A.nx) ? i : i + 1;
+  const int jm = (!A.per_y && j <= -1) ? j : j - 1, jp = (!A.per_y && j >= A.ny) ? j : j + 1;
+  const double di = Pa[pidx(m, ip, j)] - Pa[pidx(m, im, j)];
+  const double dj = Pa[pidx(m, i, jp)] - Pa[pidx(m, i, jm)];
+  const long long c = pidx(m, i, j);
+  gx = m.jinv[c] * di + m.jinv[m.pplane + c] * dj;
+  gy = m.jinv[2 * m.pplane + c] * di + m.jinv[3 * m.pplane + c] * dj;
+}
+
+// Sec 2.5 at a boundary face with outward normal (nxo, nyo) of any
+// orientation: full f (FP64).  Only directions crossing the face change.
+__device__ __forceinline__ void qface_bc(const SegParam &sp, double nxo, double nyo, double (&F)[9]) {
+  if (sp.kind == DVBE_BC_WALL_BOUNCEBACK) {
+#pragma unroll
+    for (int a = 1; a < 9; ++a)
+      if (EX(a) * nxo + EY(a) * nyo > 0)
+        F[dev::OPP(a)] = F[a] - 6.0 * WGT(a) * (EX(a) * sp.ux + EY(a) * sp.uy);
+  } else if (sp.kind == DVBE_BC_WALL_DIFFUSE) {
+    double f1[9];
+    feq9(1.0, sp.ux, sp.uy, f1);
+    double num = 0, den = 0;
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      const double en = EX(a) * nxo + EY(a) * nyo;
+      if (en > 0) num += en * F[a];
+      if (en < 0) den -= en * f1[a];
+    }
+    const double rw = num / den;
+#pragma unroll
+    for (int a = 1; a < 9; ++a)
+      if (EX(a) * nxo + EY(a) * nyo < 0) F[a] = rw * f1[a];
+  } else if (sp.kind == DVBE_BC_INFLOW_EQ) {
+    double fe[9];
+    feq9(sp.rho, sp.ux, sp.uy, fe);
+#pragma unroll
+    for (int a = 1; a < 9; ++a)
+      if (EX(a) * nxo + EY(a) * nyo < 0) F[a] = fe[a];
+  }
+}
+
+__global__ void k_qghost_x(CaseArgs A, MPArgs m) {
+  const int j = blockIdx.x * T + threadIdx.x;
+  if (j >= A.ny) return;
+  double *P = m.phi;
+  for (int side = 0; side < 2; ++side) {
+    if (A.per_x) {
+      for (int l = 1; l <= 2; ++l) {
+        const int ig = side == 0 ? -l : A.nx - 1 + l, src = side == 0 ? A.nx - l : l - 1;
+        for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, ig, j)] = P[a * m.pplane + pidx(m, src, j)];
+      }
+      continue;
+    }
+    const int ig = side == 0 ? -1 : A.nx, i1 = side == 0 ? 0 : A.nx - 1, i2 = side == 0 ? 1 : A.nx - 2;
+    double p1[9], p2[9], g[9];
+    for (int a = 0; a < 9; ++a) {
+      p1[a] = P[a * m.pplane + pidx(m, i1, j)];
+      p2[a] = P[a * m.pplane + pidx(m, i2, j)];
+      g[a] = 0.0;
+    }
+    const long long q = (long long)side * A.ny + j;
+    const SegParam &sp = A.seg[side][A.segid[side][j]];
+    if (m.qmir[q])
+      dev::apply_ghost<double, true>(sp, m.qext[q], 0.0, p1, p2, g);
+    else
+      dev::apply_ghost<double, false>(sp, m.qext[q], 0.0, p1, p2, g);
+    for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, ig, j)] = g[a];
+  }
+}
+
+__global__ void k_qghost_y(CaseArgs A, MPArgs m) {
+  const int lo = A.per_x ? -2 : -1, hi = A.per_x ? A.nx + 1 : A.nx;
+  const int i = blockIdx.x * T + threadIdx.x + lo;
+  if (i > hi) return;
+  double *P = m.phi;
+  const int ic = min(max(i, 0), A.nx - 1);
+  for (int side = 2; side < 4; ++side) {
+    if (A.per_y) {
+      for (int l = 1; l <= 2; ++l) {
+        const int jg = side == 2 ? -l : A.ny - 1 + l, src = side == 2 ? A.ny - l : l - 1;
+        for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, i, jg)] = P[a * m.pplane + pidx(m, i, src)];
+      }
+      continue;
+    }
+    const int jg = side == 2 ? -1 : A.ny, j1 = side == 2 ? 0 : A.ny - 1, j2 = side == 2 ? 1 : A.ny - 2;
+    double p1[9], p2[9], g[9];
+    for (int a = 0; a < 9; ++a) {
+      p1[a] = P[a * m.pplane + pidx(m, i, j1)];
+      p2[a] = P[a * m.pplane + pidx(m, i, j2)];
+      g[a] = 0.0;
+    }
+    const long long q = 2LL * A.ny + (long long)(side - 2) * (A.nx + 4) + (i + 2);
+    const SegParam &sp = A.seg[side][A.segid[side][ic]];
+    if (m.qmir[q])
+      dev::apply_ghost<double, true>(sp, m.qext[q], 0.0, p1, p2, g);
+    else
+      dev::apply_ghost<double, false>(sp, m.qext[q], 0.0, p1, p2, g);
+    for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, i, jg)] = g[a];
+  }
+}
+
+// One face between padded cells L = (iL, jL) and R = (iR, jR); tab[r * nf + f]
+// its tables.  Writes the nine face values phi(x_b - h xi).
+__device__ __forceinline__ void qface(const CaseArgs &A, const MPArgs &m, const double *tab,
+                                      long long nf, long long f, int iL, int jL, int iR, int jR,
+                                      bool upwind, double (&F)[9]) {
+  const double th = tab[QF_TH * nf + f], ox = tab[QF_OX * nf + f], oy = tab[QF_OY * nf + f];
+  const double dx = tab[QF_DX * nf + f], dy = tab[QF_DY * nf + f];
+  const double tx = tab[QF_TX * nf + f], ty = tab[QF_TY * nf + f];
+  const double bx = tab[QF_BX * nf + f], by = tab[QF_BY * nf + f];
+  const double nx = tab[QF_NX * nf + f], ny = tab[QF_NY * nf + f];
+  const long long L = pidx(m, iL, jL), R = pidx(m, iR, jR);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const double *Pa = m.phi + a * m.pplane;
+    const double en = EX(a) * nx + EY(a) * ny;
+    if (upwind && en != 0) {
+      double gx, gy;
+      if (en > 0) {
+        qgrad(A, m, Pa, iL, jL, gx, gy);
+        F[a] = Pa[L] + (bx - EX(a)) * gx + (by - EY(a)) * gy;
+      } else {
+        qgrad(A, m, Pa, iR, jR, gx, gy);
+        F[a] = Pa[R] + (bx - dx - EX(a)) * gx + (by - dy - EY(a)) * gy;
+      }
+      continue;
+    }
+    double glx, gly, grx, gry;
+    qgrad(A, m, Pa, iL, jL, glx, gly);
+    qgrad(A, m, Pa, iR, jR, grx, gry);
+    const double gbx = (1.0 - th) * glx + th * grx, gby = (1.0 - th) * gly + th * gry;
+    const double pb = (1.0 - th) * Pa[L] + th * Pa[R] + gbx * ox + gby * oy;
+    const double corr = (Pa[R] - Pa[L]) - (gbx * dx + gby * dy);
+    const double gfx = gbx + corr * tx, gfy = gby + corr * ty;
+    F[a] = pb - m.eshift * (EX(a) * gfx + EY(a) * gfy);
+  }
+}
+
+__global__ void k_qfaces_x(CaseArgs A, MPArgs m) {
+  const long long n = (long long)(A.nx + 1) * A.ny;
+  for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
+    const int j = (int)(t / (A.nx + 1)), k = (int)(t % (A.nx + 1));
+    const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_x || (k > 0 && k < A.nx));
+    double F[9];
+    qface(A, m, m.qfx, n, t, k - 1, j, k, j, upw, F);
+    if (!A.per_x && (k == 0 || k == A.nx)) {
+      const int side = k == 0 ? 0 : 1;
+      const double *bn = m.qbn + (long long)side * 2 * A.ny + 2 * j;
+      qface_bc(A.seg[side][A.segid[side][j]], bn[0], bn[1], F);
+    }
+    if (m.scheme == SC_DUGKS) dugks_back(A, F);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) m.fx[a * n + t] = F[a];
+  }
+}
+
+__global__ void k_qfaces_y(CaseArgs A, MPArgs m) {
+  const long long n = (long long)A.nx * (A.ny + 1);
+  for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
+    const int k = (int)(t / A.nx), i = (int)(t % A.nx);
+    const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_y || (k > 0 && k < A.ny));
+    double F[9];
+    qface(A, m, m.qfy, n, t, i, k - 1, i, k, upw, F);
+    if (!A.per_y && (k == 0 || k == A.ny)) {
+      const int side = k == 0 ? 2 : 3;
+      const double *bn = m.qbn + 4LL * A.ny + (long long)(side - 2) * 2 * A.nx + 2 * i;
+      qface_bc(A.seg[side][A.segid[side][i]], bn[0], bn[1], F);
+    }
+    if (m.scheme == SC_DUGKS) dugks_back(A, F);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) m.fy[a * n + t] = F[a];
+  }
+}
+
+// f_tilde^{n+1} = f_tilde^+ - dt c / |V| sum over the faces of (e . n_out A) f_face
+__global__ void k_qupdate(CaseArgs A, MPArgs m) {
+  const long long n = (long long)A.nx * A.ny;
+  const long long nfx = (long long)(A.nx + 1) * A.ny, nfy = (long long)A.nx * (A.ny + 1);
+  const double *ax = m.qfx + QF_AX * nfx, *ay = m.qfx + QF_AY * nfx;
+  const double *bx = m.qfy + QF_AX * nfy, *by = m.qfy + QF_AY * nfy;
+  double *fo = (double *)A.fout;
+  for (long long k = blockIdx.x * (long long)T + threadIdx.x; k < n; k += (long long)gridDim.x * T) {
+    const int j = (int)(k / A.nx), i = (int)(k % A.nx);
+    const long long w = (long long)j * (A.nx + 1) + i, s = (long long)j * A.nx + i, nn = s + A.nx;
+    const double vs = m.vs[k];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const double flux = (EX(a) * ax[w + 1] + EY(a) * ay[w + 1]) * m.fx[a * nfx + w + 1] -
+                          (EX(a) * ax[w] + EY(a) * ay[w]) * m.fx[a * nfx + w] +
+                          (EX(a) * bx[nn] + EY(a) * by[nn]) * m.fy[a * nfy + nn] -
+                          (EX(a) * bx[s] + EY(a) * by[s]) * m.fy[a * nfy + s];
+      fo[a * A.plane + (long long)j * A.pitch + i] = m.tp[a * n + k] - vs * flux;
+    }
+  }
+}
+
 int grid(long long n) {
   long long g = (n + T - 1) / T;
   return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g));
@@ -238,6 +451,15 @@ int grid(long long n) {
 
 cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s) {
   using namespace mp;
+  if (m.quad) {
+    k_stage<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+    k_qghost_x<<<grid(a.ny), T, 0, s>>>(a, m);
+    k_qghost_y<<<grid(a.nx + 4), T, 0, s>>>(a, m);
+    k_qfaces_x<<<grid((long long)(a.nx + 1) * a.ny), T, 0, s>>>(a, m);
+    k_qfaces_y<<<grid((long long)a.nx * (a.ny + 1)), T, 0, s>>>(a, m);
+    k_qupdate<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+    return cudaGetLastError();
+  }
   k_stage<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
   k_ghost_x<<<grid(a.ny), T, 0, s>>>(a, m);
   k_ghost_y<<<grid(a.nx + 4), T, 0, s>>>(a, m);

@@ -88,3 +88,43 @@ def test_validation_before_device_work(dv):
     assert _create_status(dv, dict(case, scheme=4)) == dv.DVBE_ERR_INVALID_ARG
     assert _create_status(dv, dict(case, scheme=-1)) == dv.DVBE_ERR_INVALID_ARG
     assert "CFL" in (lambda: (_create_status(dv, bad), dv.dvbe_last_error())[1])()
+
+
+def test_quad_mesh_cells_and_cfl_match_oracle(dv):
+    """dvbe_mesh_create_quad / dvbe_mesh_cells / dvbe_dt_from_cfl on
+    distorted meshes against the oracle's own quad geometry."""
+    for X, Y in (W.quad_random_interior(9, 7, 2, amp=0.3), W.quad_wavy_periodic(12, amp=0.05)):
+        ny, nx = X.shape[0] - 1, X.shape[1] - 1
+        m = dv.dvbe_mesh_create_quad(X, Y)
+        try:
+            xc, yc, vol = dv.dvbe_mesh_cells(m, nx, ny)
+            case = dict(nx=nx, ny=ny, X=X, Y=Y, RT=W.RT_LATTICE, tau=0.1, dt=0.01, bc=W.periodic_bc())
+            oxc, oyc, ovol = O.quad_geometry(case)
+            np.testing.assert_allclose(xc, oxc, rtol=0, atol=1e-15)
+            np.testing.assert_allclose(yc, oyc, rtol=0, atol=1e-15)
+            np.testing.assert_allclose(vol, ovol, rtol=1e-14)
+            assert abs(dv.dvbe_dt_from_cfl(m, W.RT_LATTICE, 0.5) / O.quad_dt_from_cfl(case, 0.5) - 1) < 1e-15
+            with pytest.raises(dv.DvbeError) as e:
+                dv.dvbe_mesh_geometry(m, nx, ny)
+            assert e.value.status == dv.DVBE_ERR_UNSUPPORTED
+        finally:
+            dv.dvbe_mesh_destroy(m)
+    # tensor meshes answer dvbe_mesh_cells too
+    xf, yf = W.tanh_faces(6, 0, 1, 1.2), W.uniform_faces(5, 0, 2)
+    m = dv.dvbe_mesh_create(xf, yf)
+    xc, yc, vol = dv.dvbe_mesh_cells(m, 6, 5)
+    dv.dvbe_mesh_destroy(m)
+    np.testing.assert_allclose(xc[0], W.centres(xf), atol=1e-15)
+    np.testing.assert_allclose(yc[:, 0], W.centres(yf), atol=1e-15)
+    np.testing.assert_allclose(vol, np.outer(np.diff(yf), np.diff(xf)), rtol=1e-15)
+
+
+def test_bad_quad_meshes_rejected(dv):
+    X, Y = W.quad_random_interior(6, 5, 1, amp=0.2)
+    for Xb, Yb in ((X[:, ::-1], Y[:, ::-1]),              # clockwise cells
+                   (np.where(np.isin(np.arange(X.size).reshape(X.shape), [9]), np.nan, X), Y)):
+        with pytest.raises(dv.DvbeError) as e:
+            dv.dvbe_mesh_create_quad(np.ascontiguousarray(Xb), np.ascontiguousarray(Yb))
+        assert e.value.status == dv.DVBE_ERR_INVALID_ARG
+    with pytest.raises(dv.DvbeError):
+        dv.dvbe_mesh_create_quad(X[:2, :1], Y[:2, :1])    # fewer than 2 cells a side

@@ -437,3 +437,26 @@ def quad_random_interior(nx: int, ny: int, seed: int, amp: float = 0.2, L=(1.0, 
     X[[0, -1], 1:-1] += amp * dx * rng.uniform(-1, 1, (2, nx - 1))
     Y[1:-1, [0, -1]] += amp * dy * rng.uniform(-1, 1, (ny - 1, 2))
     return X, Y
+
+
+def quad_min_edge(X, Y):
+    """Shortest cell edge of a vertex mesh."""
+    ex = np.hypot(np.diff(X, axis=1), np.diff(Y, axis=1))
+    ey = np.hypot(np.diff(X, axis=0), np.diff(Y, axis=0))
+    return float(min(ex.min(), ey.min()))
+
+
+def taylor_green_quad(n: int, amp: float = 0.05, u0: float = 0.01, cfl: float = 0.5,
+                      dt_over_tau: float = 10.0, scheme: str = "dugks"):
+    """The Taylor-Green box on the wavy doubly periodic n x n mesh of
+    [0, 2 pi)^2: the analytic fields at the cells' vertex-mean points, dt
+    from the CFL number on the shortest edge, tau = dt / dt_over_tau."""
+    X, Y = quad_wavy_periodic(n, L=2 * math.pi, amp=amp)
+    x = 0.25 * (X[:-1, :-1] + X[:-1, 1:] + X[1:, 1:] + X[1:, :-1])
+    y = 0.25 * (Y[:-1, :-1] + Y[:-1, 1:] + Y[1:, 1:] + Y[1:, :-1])
+    dt = cfl * quad_min_edge(X, Y) / math.sqrt(6.0 * RT_LATTICE)
+    tau = dt / dt_over_tau
+    case = dict(nx=n, ny=n, X=X, Y=Y, RT=RT_LATTICE, tau=tau, dt=dt, scheme=scheme, bc=periodic_bc(),
+                nu=tau * RT_LATTICE, u0=u0, name=f"taylor-green wavy quad {n}x{n}")
+    rho = 1.0 - u0 * u0 * (np.cos(2 * x) + np.cos(2 * y)) / 4.0 / RT_LATTICE
+    return case, (rho, -u0 * np.cos(x) * np.sin(y), u0 * np.sin(x) * np.cos(y))
