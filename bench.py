@@ -71,6 +71,12 @@ def workload_config(a):
             "scheme": a.scheme, "precision": a.precision, "cells": a.n * a.n}
 
 
+def step_kernels(scheme, precision):
+    """Name of the kernels of one fused step: the inner strips and the edge
+    strips, launched concurrently on two streams."""
+    return f"k_step_inner + k_step_edge<{scheme}, {precision}>"
+
+
 def measured_traffic(scheme, precision, cells):
     """DRAM bytes per launch of the headline kernel from the committed ncu
     capture (profiles/traffic.json), scaled to this mesh; None if the capture
@@ -83,7 +89,7 @@ def measured_traffic(scheme, precision, cells):
             sha = hashlib.sha256(f.read()).hexdigest()
     except Exception:
         return None
-    if t["kernel"] != f"k_step<{scheme}, {precision}>" or not sha.startswith(t["sha256_prefix"]):
+    if t["kernel"] != step_kernels(scheme, precision) or not sha.startswith(t["sha256_prefix"]):
         return None
     return t["dram_bytes_per_cell"] * cells
 
@@ -550,7 +556,7 @@ def main():
                          "traffic": measured_traffic(a.scheme, a.precision, cells),
                          "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL[a.precision],
-                         "kernel": f"k_step<{a.scheme}, {a.precision}>"},
+                         "kernel": step_kernels(a.scheme, a.precision)},
             "accuracy": acc,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -40,7 +40,9 @@ def run(dv, scheme, stretched, precision):
     case, fields = W.cavity(256, Re=1000, U=0.1, cfl=0.5, scheme=scheme,
                             stretch_beta=1.5 if stretched else None)
     with dv.Solver(case, precision=precision) as s:
-        s.set_launch(strip_rows=16, graph_chunk=500)
+        s.init_equilibrium(*fields)
+        s.autotune(20)  # on 256^2 the launch shape sets how full the GPU is
+        s.set_launch(graph_chunk=500)
         s.init_equilibrium(*fields)
         m0 = s.conserved()[0]
         s.residual()
