@@ -292,13 +292,19 @@ DVBE_API dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms);
  * Process-wide. */
 DVBE_API dvbe_status dvbe_set_autotune_cache(const char *path);
 
-/* Device view of the current f_tilde (for timing and inspection): base
- * pointer, row pitch in elements, elements per field, element size. */
+/* Device view of the current f_tilde (for timing and inspection): pointer to
+ * column 0 of row 0 of field 0, row pitch in elements, elements per field,
+ * element size; element (a, j, i) is at ptr + a * plane + j * pitch + i.  On
+ * a mesh periodic in x the rows carry halo columns (copies of the columns at
+ * the other end) just before column 0 and just after column nx-1. */
 DVBE_API dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch,
                               long long *plane, int *elem_bytes);
 /* Kernel launches issued since creation (every step kernel, init, reduction).
- * A step is one launch, or two on meshes with inner strips: the strips that
- * touch no boundary run in a kernel compiled without boundary code. */
+ * A step is one launch, or two on meshes with inner strips and boundary
+ * strips: the strips that touch no boundary run in a kernel compiled without
+ * boundary code, the others in a second kernel at the same time.  On a mesh
+ * periodic in both directions every strip is inner (one launch), except for
+ * FP32 and 16-bit storage at an odd nx. */
 DVBE_API dvbe_status dvbe_launch_count(dvbe_solver s, long long *count);
 
 /* Spatial decomposition (the paper has none; its FV form on cells V_k and

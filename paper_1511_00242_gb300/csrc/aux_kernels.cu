@@ -308,6 +308,33 @@ cudaError_t aux_fill_rest(const FieldView &v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename E> __global__ void k_fill_halo(FieldView v, int hx) {
+  const long long n = 9LL * v.ny * 2 * hx;
+  E *f = (E *)v.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % (2 * hx));
+    const long long r = t / (2 * hx);
+    const int j = (int)(r % v.ny), a = (int)(r / v.ny);
+    E *row = f + (long long)a * v.plane + (long long)j * v.pitch;
+    if (q < hx)
+      row[q - hx] = row[v.nx - hx + q];
+    else
+      row[v.nx + (q - hx)] = row[q - hx];
+  }
+}
+
+cudaError_t aux_fill_halo(const FieldView &v, int hx, cudaStream_t s) {
+  const long long n = 9LL * v.ny * 2 * hx;
+  if (v.store == ST_F64)
+    k_fill_halo<double><<<grid_for(n), 256, 0, s>>>(v, hx);
+  else if (v.store == ST_F16_DEV || v.store == ST_BF16_DEV)
+    k_fill_halo<unsigned short><<<grid_for(n), 256, 0, s>>>(v, hx);
+  else
+    k_fill_halo<float><<<grid_for(n), 256, 0, s>>>(v, hx);
+  return cudaGetLastError();
+}
+
 cudaError_t aux_set_field(const FieldView &v, int a, const double *src, cudaStream_t s) {
   k_set_field<<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(v, a, src);
   return cudaGetLastError();

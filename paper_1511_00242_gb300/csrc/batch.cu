@@ -141,7 +141,7 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
   }
   dvbe_status st = DVBE_OK;
   for (int c = 0; c < ncases && st == DVBE_OK; ++c) {
-    st = build_problem(&cases[c], b->pb[c]);
+    st = build_problem(&cases[c], b->pb[c], true);
     if (st == DVBE_OK && b->pb[c].kernel == SC_BKG_FD)
       st = fail(DVBE_ERR_UNSUPPORTED, "the batched form runs BKG in finite-volume form only");
     if (st == DVBE_OK && b->pb[c].kernel == SC_CFREE)
@@ -163,6 +163,10 @@ dvbe_status dvbe_batch_create(const dvbe_params *cases, int ncases, dvbe_batch *
       FieldView v = view_of(b->pb[c], b->f[0][c]);
       e = aux_fill_rest(v, b->stream);
       b->launches += 1;
+      if (e == cudaSuccess && b->pb[c].hx > 0) {
+        e = aux_fill_halo(v, b->pb[c].hx, b->stream);
+        b->launches += 1;
+      }
       if (e != cudaSuccess) st = cuda_fail(e, "batch initialisation");
     }
   }
@@ -207,6 +211,10 @@ dvbe_status dvbe_batch_init_equilibrium(dvbe_batch b, int c, const double *rho, 
   if (st != DVBE_OK) return st;
   cudaError_t e = aux_init_eq(view_of(b->pb[c], b->f[b->cur][c]), d, d + n, d + 2 * n, b->stream);
   b->launches += 1;
+  if (e == cudaSuccess && b->pb[c].hx > 0) {
+    e = aux_fill_halo(view_of(b->pb[c], b->f[b->cur][c]), b->pb[c].hx, b->stream);
+    b->launches += 1;
+  }
   unsigned z = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->flags + c, &z, sizeof z, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -66,6 +66,7 @@ struct Problem {
   bool quad = false;           // quadrilateral mesh (multi-pass step only)
   QuadHost q;
   int pitch = 0, elem = 0;
+  int hx = 0;                  // halo columns of a row (CaseArgs::hx)
   long long plane = 0;
 };
 
@@ -115,7 +116,9 @@ dvbe_status fail(dvbe_status st, const std::string &msg);
 dvbe_status cuda_fail(cudaError_t e, const char *what);
 void *dmalloc(size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
-dvbe_status build_problem(const dvbe_params *p, Problem &pb);
+// halo: lay the rows out with halo columns when the mesh is periodic in x
+// and the fused step runs (CaseArgs::hx).
+dvbe_status build_problem(const dvbe_params *p, Problem &pb, bool halo = false);
 dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cudaStream_t s);
 void set_strips(CaseArgs &a, int H, int store);
 // Kernel launches of one step (two when the inner strips run in their own kernel).

@@ -117,7 +117,7 @@ static int find_seg(const std::vector<dvbe_bc_segment> &segs, double t) {
 
 static double c_lat(const Problem &pb) { return std::sqrt(3.0 * pb.RT); }
 
-dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
+dvbe_status build_problem(const dvbe_params *p, Problem &pb, bool halo) {
   if (!p) return fail(DVBE_ERR_INVALID_ARG, "params is NULL");
   if (!p->mesh) return fail(DVBE_ERR_INVALID_ARG, "params.mesh is NULL");
   const dvbe_mesh_ &m = *p->mesh;
@@ -325,7 +325,13 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb) {
   // staged row box (at most 40 elements) always fits inside a row
   const int eb = elem_bytes(pb.store);
   const int align = 128 / eb;
-  pb.pitch = std::max(((nx + align - 1) / align) * align, 64);
+  // halo columns (CaseArgs::hx): one 16-byte group on each side, so that the
+  // row copies stay aligned; a lane's columns must not straddle the end of
+  // the row, and the two copies must not overlap
+  pb.hx = 0;
+  if (halo && DVBE_HALO && pb.per_x && !pb.multipass && nx % lane_cols(pb.store) == 0 && nx >= 2 * (16 / eb))
+    pb.hx = 16 / eb;
+  pb.pitch = std::max(((nx + 2 * pb.hx + align - 1) / align) * align, 64);
   pb.plane = (long long)pb.pitch * ny;
   pb.elem = eb;
   // the step kernel addresses f_tilde with 32-bit element offsets
@@ -386,6 +392,7 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   a.wait_limit = kDefaultWaitLimit;
   a.plane = pb.plane;
   a.pitch = pb.pitch;
+  a.hx = pb.hx;
   a.nx = pb.nx;
   a.ny = pb.ny;
   a.per_x = pb.per_x;
@@ -431,6 +438,10 @@ void set_strips(CaseArgs &a, int H, int store) {
   const int symax = (a.ny - 1) / H - 1;
   a.in_x0 = 1;
   a.in_nx = std::max(0, sxmax);
+  if (a.hx > 0) { // halo columns: every column strip reads its wrap neighbours as cells
+    a.in_x0 = 0;
+    a.in_nx = a.strips_x;
+  }
   a.in_y0 = a.per_y ? 0 : 1;
   a.in_ny = a.per_y ? a.strips_y : std::max(0, symax);
   a.He = H;
@@ -457,7 +468,7 @@ int kernels_per_step(const CaseArgs &a) {
 
 FieldView view_of(const Problem &pb, void *f) {
   FieldView v;
-  v.f = f;
+  v.f = (char *)f + (size_t)pb.hx * pb.elem; // column 0 of row 0 of field 0
   v.plane = pb.plane;
   v.pitch = pb.pitch;
   v.nx = pb.nx;
@@ -782,7 +793,7 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
   *out = nullptr;
   dvbe_solver s = new (std::nothrow) dvbe_solver_;
   if (!s) return fail(DVBE_ERR_OOM, "host allocation failed");
-  dvbe_status st = build_problem(p, s->pb);
+  dvbe_status st = build_problem(p, s->pb, true);
   if (st != DVBE_OK) {
     delete s;
     return st;
@@ -829,9 +840,13 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, fbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->flag, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = aux_fill_rest(cur_view(s), s->stream);
+    s->launches += 1;
+    if (e == cudaSuccess && s->pb.hx > 0) {
+      e = aux_fill_halo(cur_view(s), s->pb.hx, s->stream);
+      s->launches += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "solver initialisation");
-    s->launches += 1;
   }
   if (st != DVBE_OK) {
     dvbe_solver_destroy(s);
@@ -844,6 +859,10 @@ dvbe_status dvbe_solver_create(const dvbe_params *p, dvbe_solver *out) {
 }
 
 static dvbe_status after_init(dvbe_solver s, cudaError_t e, const char *what) {
+  if (e == cudaSuccess && s->pb.hx > 0) { // the halo copies of the new state
+    e = aux_fill_halo(cur_view(s), s->pb.hx, s->stream);
+    s->launches += 1;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, what);
   s->steps = 0;
@@ -1233,7 +1252,7 @@ dvbe_status dvbe_autotune(dvbe_solver s, int steps, double *best_ms) {
 dvbe_status dvbe_device_state(dvbe_solver s, void **ptr, long long *pitch, long long *plane,
                               int *elem_bytes_) {
   if (!s) return fail(DVBE_ERR_INVALID_ARG, "NULL solver");
-  if (ptr) *ptr = s->f[s->cur];
+  if (ptr) *ptr = cur_view(s).f;
   if (pitch) *pitch = s->pb.pitch;
   if (plane) *plane = s->pb.plane;
   if (elem_bytes_) *elem_bytes_ = s->pb.elem;
@@ -1254,6 +1273,10 @@ static dvbe_status copy_line(dvbe_solver s, int axis, int index, int lo, int hi,
     return fail(DVBE_ERR_INVALID_ARG, std::string(what) + ": line outside the mesh");
   cudaError_t e = aux_copy_line(cur_view(s), s->pb.elem, axis, index, lo, hi - lo, buf, to_buf, s->stream);
   s->launches += 1;
+  if (e == cudaSuccess && !to_buf && s->pb.hx > 0) { // cells may have changed under their copies
+    e = aux_fill_halo(cur_view(s), s->pb.hx, s->stream);
+    s->launches += 1;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, what);
   return DVBE_OK;

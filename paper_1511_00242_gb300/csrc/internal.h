@@ -19,6 +19,12 @@ enum StoreMode { ST_F64 = 0, ST_F32 = 1, ST_F32_DEV = 2, ST_F16_DEV = 3, ST_BF16
 // and used as the flux distribution; central = zero slopes in the tables).
 enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2, SC_CFREE = 3 };
 
+// Halo columns for meshes periodic in x (CaseArgs::hx); 0 keeps plain rows
+// and the wrap copies of the edge strips.
+#ifndef DVBE_HALO
+#define DVBE_HALO 1
+#endif
+
 // Strip geometry.  A warp's lanes hold lane_cols adjacent columns each (two
 // for FP32 arithmetic, which then issues paired FP32 instructions; one for
 // FP64); NC halo columns on each side leave strip_cols output columns per
@@ -55,6 +61,13 @@ struct CaseArgs {
   void *fout;
   long long plane; // elements per field
   int pitch;       // elements per row
+  // Halo columns of a mesh periodic in x (0: none).  Column i of a row sits
+  // at element hx + i of it; elements 0 .. hx-1 hold copies of columns
+  // nx-hx .. nx-1 and elements nx+hx .. nx+2hx-1 copies of columns 0 ..
+  // hx-1, written by the step with the columns themselves.  The row copies
+  // of the step read across the wrap from them, so no strip needs wrap code.
+  // fin / fout and the tensor maps address the rows from element 0.
+  int hx;
   int nx, ny;
   int per_x, per_y;
   int strips_x, strips_y, H; // strip decomposition: strip_cols columns x H rows per warp
@@ -133,6 +146,10 @@ cudaError_t aux_init_ce(const FieldView &v, const double *d_rho, const double *d
                         const double *d_uy, const double *const *d_deriv, cudaStream_t s);
 // f_tilde = w_alpha rho0 (fluid at rest)
 cudaError_t aux_fill_rest(const FieldView &v, cudaStream_t s);
+// The halo columns of every row and field (CaseArgs::hx = hx of them on each
+// side; v.f addresses column 0) refreshed from the columns they copy:
+// columns -hx .. -1 from nx-hx .. nx-1, columns nx .. nx+hx-1 from 0 .. hx-1.
+cudaError_t aux_fill_halo(const FieldView &v, int hx, cudaStream_t s);
 // one field alpha: double [ny][nx] <-> storage
 cudaError_t aux_set_field(const FieldView &v, int alpha, const double *d_src, cudaStream_t s);
 cudaError_t aux_get_field(const FieldView &v, int alpha, double *d_dst, cudaStream_t s);

@@ -660,6 +660,11 @@ template <int SCHEME, int ST> struct Strip {
   uint32_t offc[NC]; // byte offset of each column inside a stage (boundary strips)
   uint32_t lds_off;  // byte offset of the first column (inner strips: one aligned load)
   bool per_x, per_y, touchW, touchE, wrapW, wrapE, out_lane;
+  // halo columns (A.hx > 0): this strip writes some of them, and this lane
+  // writes the copy of its columns at +nx (columns 0 .. hx-1) or -nx
+  // (columns nx-hx .. nx-1); inner strips store a lane's columns whole
+  bool hstrip, hlo, hhi;
+  int xsp; // staged start in the row copy's coordinates (xs + hx)
   V b_phi;       // phi = d + b_phi (d_eq - d)
   V q_face;      // DUGKS face: f = f_bar + q (f_eq - f_bar)
   // x-face coefficients of this lane's columns: right part of the west face,
@@ -720,12 +725,20 @@ template <int SCHEME, int ST> struct Strip {
     c0 = i0 - NC + NC * lane;
     touchW = !per_x && i0 == 0;
     touchE = !per_x && i0 + COLS >= nx;
-    wrapW = per_x && i0 == 0;
-    wrapE = per_x && i0 + COLS >= nx;
-    out_lane = lane >= 1 && lane <= 30; // inner strips: these lanes hold outputs only
+    const int hx = A.hx;
+    wrapW = per_x && i0 == 0 && hx == 0;
+    wrapE = per_x && i0 + COLS >= nx && hx == 0;
+    // inner strips: lanes 1 .. 30 hold outputs only, all of a lane's columns
+    // at once (with halo columns the last strip may end inside a warp; nx is
+    // then a multiple of NC)
+    out_lane = lane >= 1 && lane <= 30 && c0 + NC - 1 < nx;
+    hstrip = hx > 0 && (i0 < hx || i0 + COLS > nx - hx);
+    hlo = out_lane && c0 < hx;
+    hhi = out_lane && c0 >= nx - hx;
     // staged columns: [xs, xs + W) with xs the aligned start at or left of i0 - NC
     const int al = 16 / ES;
     xs = (i0 - NC >= 0) ? ((i0 - NC) / al) * al : -al;
+    xsp = xs + hx;
     lds_off = (uint32_t)((c0 - xs) * ES);
     xwrapW = ((nx - 1) / al) * al;
     txbytes = 9u * P::W * ES + (wrapW ? 9u * 16u : 0u) + (wrapE ? 9u * 16u : 0u);
@@ -793,7 +806,7 @@ template <int SCHEME, int ST> struct Strip {
       ky2 = Real(0.5) * nuy * nuy;
       kxy = Real(0.25) * nux * nuy;
     }
-    fout = (T *)A.fout;
+    fout = (T *)A.fout + hx;
     pitch = (unsigned)A.pitch;
     plane = (unsigned)A.plane;
   }
@@ -803,7 +816,7 @@ template <int SCHEME, int ST> struct Strip {
     if (timeout) return;
     const uint32_t bar = bbase + 8 * islot, dst = sbase + islot * P::STAGEB;
     const int r = wrapr(Fa + nissued); // periodic in y: rows -1 and ny wrap
-    tma_row_pred((uint32_t)(lane == 0), bar, txbytes, dst, &A.tm_main, xs, r);
+    tma_row_pred((uint32_t)(lane == 0), bar, txbytes, dst, &A.tm_main, xsp, r);
     if (!INT && (wrapW || wrapE)) {
       if (lane == 0) {
         if (wrapW) tma_load3(dst + P::MAINB, &A.tm_wrap, xwrapW, r, 0, bar);
@@ -1043,12 +1056,26 @@ template <int SCHEME, int ST> struct Strip {
       const unsigned off = (unsigned)j * pitch + (unsigned)c0;
 #pragma unroll
       for (int a = 0; a < 9; ++a) st_lane(fout + (off + a * plane), encode<ST>(v[a], a, k), out_lane);
+      if (hstrip) { // warp-uniform: the strips at the two ends of a halo row
+        // copies at c0 + nx (hlo) or c0 - nx (hhi): signed, both inside the row
+        const int hoff = hlo ? nx : -nx;
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+          st_lane(fout + ((long long)(off + a * plane) + hoff), encode<ST>(v[a], a, k), hlo || hhi);
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const unsigned off = (unsigned)j * pitch + (unsigned)min(max(col[c], 0), nx - 1);
 #pragma unroll
         for (int a = 0; a < 9; ++a) st_pred(fout + (off + a * plane), comp(encode<ST>(v[a], a, k), c), outc[c]);
+        if (hstrip) {
+          const bool lo = outc[c] && col[c] < A.hx, hi = outc[c] && col[c] >= nx - A.hx;
+          const int hoff = lo ? nx : -nx;
+#pragma unroll
+          for (int a = 0; a < 9; ++a)
+            st_pred(fout + ((long long)(off + a * plane) + hoff), comp(encode<ST>(v[a], a, k), c), lo || hi);
+        }
       }
     }
   }
@@ -1255,7 +1282,8 @@ template <int SCHEME, int ST> struct Strip {
     } else {
       // inner strip: its columns i0 - 1 .. i0 + COLS are cells, and so are the
       // rows j0-1 .. jend, or the mesh is periodic in y (rows wrap)
-      const bool inner = i0 >= 1 && i0 + COLS <= nx - 1 && (per_y || (j0 >= 1 && jend <= ny - 1));
+      const bool cols_inner = A.hx > 0 || (i0 >= 1 && i0 + COLS <= nx - 1);
+      const bool inner = cols_inner && (per_y || (j0 >= 1 && jend <= ny - 1));
       if (inner)
         run_t<true>(j0, jend);
       else

@@ -55,7 +55,11 @@ def test_inner_and_ring_kernels(dv, scheme, H, walls):
             s.init_f(s.get_f() + delta)
             l0 = s.launch_count()
             s.step(12)
-            assert s.launch_count() - l0 == 24  # inner kernel and ring kernel per step
+            # inner kernel and ring kernel per step; a mesh periodic in x keeps
+            # halo columns (FP64 at any width, pairs of FP32 columns at even
+            # widths) and then every strip is inner
+            halo = not walls and (precision == "f64" or nx % 2 == 0)
+            assert s.launch_count() - l0 == (12 if halo else 24)
             g = s.get_f()
         if precision == "f64":
             assert float(np.max(np.abs(g - o) / np.abs(o))) < 1e-12

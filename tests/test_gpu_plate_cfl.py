@@ -3,9 +3,13 @@ set-up: U = 0.1, L = 1, Re_L = 1e5, y cells growing geometrically from
 dy_min = L / 5000), FP32 arithmetic with FP32-deviation storage, DUGKS
 against BKG at CFL 0.1, 0.5, 0.9 and 0.95.  After 2.5 flow-through times the
 u profiles at x = 0.2 L and 0.6 L are compared with the Blasius solution
-(max |u / U - f'| over eta < 5).  DUGKS follows Blasius at every CFL number;
-BKG's error grows with the time step (its numerical dissipation is
-proportional to dt, Sec 2.4) or it diverges near CFL 1."""
+(max |u / U - f'| over eta < 5).  Measured on GB300: DUGKS within 1.3% of U
+at every CFL number, its error falling as the CFL number grows (0.0077 ->
+0.0048 at x = 0.2 L); BKG within 1.4%, its error at x = 0.2 L growing with
+the time step (0.0079 at CFL 0.1 -> 0.0101 at 0.95; its numerical
+dissipation is proportional to dt, Sec 2.4) and above DUGKS's from CFL 0.5
+on.  On this mesh (29 cells inside eta < 5 at x = 0.2 L, 44 at 0.6 L) neither
+scheme deviates as BKG does on the paper's coarsest mesh."""
 import math
 
 import numpy as np
@@ -62,10 +66,12 @@ def test_plate_512x256_cfl_sweep(dv):
             out[(scheme, cfl)] = err
             msg = "diverged" if err is None else f"x=0.2L {err[0]:.4f}, x=0.6L {err[1]:.4f}"
             print(f"plate 512x256 {scheme} CFL {cfl} ({steps} steps): max |u/U - f'| {msg}")
-    for cfl in (0.1, 0.5, 0.9, 0.95):
-        assert out[("dugks", cfl)] is not None and max(out[("dugks", cfl)]) < 0.05, (cfl, out)
-    b01 = out[("bkg", 0.1)]
-    assert b01 is not None
-    for cfl in (0.5, 0.9, 0.95):
-        b = out[("bkg", cfl)]
-        assert b is None or max(b) > max(b01), (cfl, out)
+    cfls = (0.1, 0.5, 0.9, 0.95)
+    assert all(out[k] is not None for k in out), out
+    for cfl in cfls:
+        assert max(out[("dugks", cfl)]) < 0.015, (cfl, out)
+        assert max(out[("bkg", cfl)]) < 0.02, (cfl, out)
+    b = [out[("bkg", c)][0] for c in cfls]
+    assert all(b[k] < b[k + 1] for k in range(3)), b  # BKG at x = 0.2 L: worse as dt grows
+    for cfl in cfls[1:]:
+        assert out[("dugks", cfl)][0] < out[("bkg", cfl)][0], (cfl, out)
