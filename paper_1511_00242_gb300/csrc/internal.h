@@ -105,6 +105,7 @@ struct CaseArgs {
   SegParam seg[4][DVBE_MAX_SEGMENTS];
 
   unsigned int *flag; // bit 0: divergence seen; bit 1: a bounded wait ran out
+  int walls_only;     // every non-periodic side is a bounce-back or diffuse wall
 };
 
 // Default of CaseArgs::wait_limit.

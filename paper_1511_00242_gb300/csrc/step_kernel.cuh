@@ -58,10 +58,10 @@
 #define DVBE_BKG_UNROLL 1
 #endif
 #ifndef DVBE_PAIR_DUGKS_UNROLL
-#define DVBE_PAIR_DUGKS_UNROLL 0
+#define DVBE_PAIR_DUGKS_UNROLL 1
 #endif
 #ifndef DVBE_PAIR_BKG_UNROLL
-#define DVBE_PAIR_BKG_UNROLL 0
+#define DVBE_PAIR_BKG_UNROLL 1
 #endif
 // The ring kernel of the two-kernel step: 1 = on the side stream beside the
 // inner kernel, 0 = after it on the main stream; DVBE_RING_FIRST 1 launches
@@ -338,8 +338,14 @@ __device__ __forceinline__ void cell_deq(V rp, V rho, V mx, V my, V Ux, V Uy, V 
   deq[6] = vfma(r2, Qm, p2 - gm); // e = (-1, +1)
 }
 
+// Boundary rules compiled into the general path: all kinds, or walls only
+// (bounce-back and diffuse; periodic sides need no rule).  A smaller general
+// path keeps the boundary strips of wall-bounded meshes in the instruction
+// cache.
+enum { BCS_ALL = 0, BCS_WALLS = 1 };
+
 // Ghost rule for one ghost cell from the first (p1) and second (p2) inner cell.
-template <typename Real, bool XSIDE>
+template <typename Real, bool XSIDE, int BCS = BCS_ALL>
 __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho0,
                                             const Real (&p1)[9], const Real (&p2)[9],
                                             Real (&g)[9]) {
@@ -347,15 +353,15 @@ __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho
   if (kind == DVBE_BC_WALL_BOUNCEBACK || kind == DVBE_BC_WALL_DIFFUSE) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = p1[a] + e * (p1[a] - p2[a]);
-  } else if (kind == DVBE_BC_INFLOW_EQ) {
+  } else if (BCS == BCS_ALL && kind == DVBE_BC_INFLOW_EQ) {
     Real rho = Real(sp.rho), Ux = Real(sp.ux), Uy = Real(sp.uy);
     Real u15 = Real(1.5) * (Ux * Ux + Uy * Uy);
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = deq_of<Real>(a, rho - rho0, rho, Ux, Uy, u15);
-  } else if (kind == DVBE_BC_OUTFLOW_ZG) {
+  } else if (BCS == BCS_ALL && kind == DVBE_BC_OUTFLOW_ZG) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = p1[a];
-  } else if (kind == DVBE_BC_OUTFLOW_NEQ) {
+  } else if (BCS == BCS_ALL && kind == DVBE_BC_OUTFLOW_NEQ) {
     // the first inner value with its equilibrium part at the segment's
     // density: g = p1 + f_eq(rho_s, U_1) - f_eq(rho_1, U_1)
     //            = p1 + w (rho_s - rho_1) (1 + P(U_1))
@@ -374,7 +380,7 @@ __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho
       const Real P = eU * (Real(3) + Real(4.5) * eU) - u15;
       g[a] = p1[a] + Real(WGT(a)) * dr * (Real(1) + P);
     }
-  } else if (kind == DVBE_BC_SYMMETRY) {
+  } else if (BCS == BCS_ALL && kind == DVBE_BC_SYMMETRY) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) g[a] = p1[XSIDE ? MIRX(a) : MIRY(a)];
   }
@@ -383,7 +389,7 @@ __device__ __forceinline__ void apply_ghost(const SegParam &sp, Real e, Real rho
 // Boundary face treatment (Sec 2.5) on face values fb (deviations), outward
 // normal (nx_o, ny_o) of the fluid.  Only the directions crossing the face
 // are read or written.
-template <typename Real>
+template <typename Real, int BCS = BCS_ALL>
 __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Real rho0,
                                         Real (&fb)[9]) {
   const int kind = sp.kind;
@@ -414,7 +420,7 @@ __device__ __forceinline__ void face_bc(const SegParam &sp, int nxo, int nyo, Re
     for (int a = 1; a < 9; ++a) {
       if (EX(a) * nxo + EY(a) * nyo < 0) fb[a] = rw * f1[a] - Real(WGT(a)) * rho0;
     }
-  } else if (kind == DVBE_BC_INFLOW_EQ) {
+  } else if (BCS == BCS_ALL && kind == DVBE_BC_INFLOW_EQ) {
     // free stream: the distributions entering the domain are f_eq of the
     // free-stream state; those leaving keep their reconstructed values
     Real rho = Real(sp.rho), Ux = Real(sp.ux), Uy = Real(sp.uy);
@@ -637,7 +643,7 @@ template <int ES, int NC> struct Pipe {
 
 // ---- the strip ---------------------------------------------------------------
 
-template <int SCHEME, int ST> struct Strip {
+template <int SCHEME, int ST, int BCS = BCS_ALL> struct Strip {
   using S = StoreT<ST>;
   using Real = typename S::Real;
   using T = typename S::T;
@@ -930,7 +936,7 @@ template <int SCHEME, int ST> struct Strip {
           get(q1, c, s1);
           get(q2, c, s2);
           get(phi, c, g);
-          apply_ghost<Real, true>(A.seg[0][A.segid[0][r]], Real(A.ext[0]), comp(k.rho0, 0), s1, s2, g);
+          apply_ghost<Real, true, BCS>(A.seg[0][A.segid[0][r]], Real(A.ext[0]), comp(k.rho0, 0), s1, s2, g);
           put(phi, c, g);
         }
       }
@@ -948,7 +954,7 @@ template <int SCHEME, int ST> struct Strip {
           get(q1, c, s1);
           get(q2, c, s2);
           get(phi, c, g);
-          apply_ghost<Real, true>(A.seg[1][A.segid[1][r]], Real(A.ext[1]), comp(k.rho0, 0), s1, s2, g);
+          apply_ghost<Real, true, BCS>(A.seg[1][A.segid[1][r]], Real(A.ext[1]), comp(k.rho0, 0), s1, s2, g);
           put(phi, c, g);
         }
       }
@@ -964,7 +970,7 @@ template <int SCHEME, int ST> struct Strip {
       get(p2, c, s2);
       get(g, c, gs);
       const SegParam &sp = A.seg[side][side == 2 ? segS[c] : segN[c]];
-      apply_ghost<Real, false>(sp, Real(A.ext[side]), comp(k.rho0, 0), s1, s2, gs);
+      apply_ghost<Real, false, BCS>(sp, Real(A.ext[side]), comp(k.rho0, 0), s1, s2, gs);
       put(g, c, gs);
     }
   }
@@ -1001,7 +1007,7 @@ template <int SCHEME, int ST> struct Strip {
           const int side = col[c] == 0 ? 0 : 1;
           Real s[9];
           get(F, c, s);
-          face_bc<Real>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, comp(k.rho0, 0), s);
+          face_bc<Real, BCS>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, comp(k.rho0, 0), s);
           put(F, c, s);
         }
       }
@@ -1042,7 +1048,7 @@ template <int SCHEME, int ST> struct Strip {
       for (int c = 0; c < NC; ++c) {
         Real sv[9];
         get(F, c, sv);
-        face_bc<Real>(A.seg[side][side == 2 ? segS[c] : segN[c]], 0, side == 2 ? -1 : 1,
+        face_bc<Real, BCS>(A.seg[side][side == 2 ? segS[c] : segN[c]], 0, side == 2 ? -1 : 1,
                       comp(k.rho0, 0), sv);
         put(F, c, sv);
       }
@@ -1376,15 +1382,16 @@ template <int PART> __host__ __device__ constexpr int part_paths() {
 }
 
 // The strips of one part, each warp taking items gw, gw + nw, ...
-template <int SCHEME, int ST, int PART> __device__ __forceinline__ void step_part(const CaseArgs &A) {
+template <int SCHEME, int ST, int PART, int BCS = BCS_ALL>
+__device__ __forceinline__ void step_part(const CaseArgs &A) {
   extern __shared__ __align__(128) unsigned char smem[];
-  using P = typename Strip<SCHEME, ST>::P;
+  using P = typename Strip<SCHEME, ST, BCS>::P;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long nitems = part_items<PART>(A);
-  Strip<SCHEME, ST> s(A, lane, smem_u32(smem) + wib * P::WARPB);
+  Strip<SCHEME, ST, BCS> s(A, lane, smem_u32(smem) + wib * P::WARPB);
   s.init_barriers();
   for (long long it = gw; it < nitems; it += nw) {
     int sx, j0, jend;
@@ -1424,9 +1431,9 @@ __global__ void __maxnreg__((inner_maxreg<SCHEME, ST>())) k_step_inner(const __g
 }
 // The ring of boundary strips: the general path alone also fits the cap
 // with little spilling, so it too runs at the inner kernel's occupancy.
-template <int SCHEME, int ST>
+template <int SCHEME, int ST, int BCS>
 __global__ void __maxnreg__((inner_maxreg<SCHEME, ST>())) k_step_edge(const __grid_constant__ CaseArgs A) {
-  step_part<SCHEME, ST, PART_EDGE>(A);
+  step_part<SCHEME, ST, PART_EDGE, BCS>(A);
 }
 
 // Batched form: warps take strips of all cases from one queue.
@@ -1515,7 +1522,8 @@ cudaError_t launch_step_scheme(const CaseArgs &a, int blocks, int wpb, const Ste
     return cudaGetLastError();
   }
   auto ki = dev::k_step_inner<SCHEME, ST>;
-  auto ke = dev::k_step_edge<SCHEME, ST>;
+  // a mesh whose non-periodic sides are walls only: the smaller general path
+  auto ke = a.walls_only ? dev::k_step_edge<SCHEME, ST, dev::BCS_WALLS> : dev::k_step_edge<SCHEME, ST, dev::BCS_ALL>;
   e = allow_smem(ki, smem);
   if (e == cudaSuccess) e = allow_smem(ke, smem);
   if (e != cudaSuccess) return e;
