@@ -306,7 +306,7 @@ def case_throughput(dv, stream, torch, case, fields, precision, steps, peak, pat
     s = dv.Solver(case, precision=precision, stream=stream.cuda_stream, path=path)
     try:
         s.init_equilibrium(*fields)
-        s.autotune(10)
+        s.autotune(30)  # short meshes and several kernels: 10 steps per shape is too noisy
         s.step(5)
         t, _ = time_steps(dv, s, stream, torch, steps)
         cells = case["nx"] * case["ny"]

@@ -41,7 +41,8 @@ def _stale(target: str, deps) -> bool:
 
 KNOBS = ("DVBE_DUGKS_MINB", "DVBE_BKG_MINB", "DVBE_DUGKS_UNROLL", "DVBE_BKG_UNROLL",
          "DVBE_PAIR_MINB", "DVBE_PAIR_DUGKS_UNROLL", "DVBE_PAIR_BKG_UNROLL", "DVBE_STAGES",
-         "DVBE_PAIR_INNER_MAXREG", "DVBE_RING_CONCURRENT", "DVBE_RING_FIRST", "DVBE_RING_PRIORITY", "DVBE_HALO")
+         "DVBE_PAIR_INNER_MAXREG", "DVBE_RING_CONCURRENT", "DVBE_RING_FIRST", "DVBE_RING_PRIORITY", "DVBE_HALO",
+         "DVBE_WALLS_PATH")
 
 
 def _build_id(extra):

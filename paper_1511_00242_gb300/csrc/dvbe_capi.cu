@@ -393,7 +393,7 @@ dvbe_status upload_problem(const Problem &pb, DeviceProblem &dp, CaseArgs &a, cu
   a.plane = pb.plane;
   a.pitch = pb.pitch;
   a.hx = pb.hx;
-  a.walls_only = 1;
+  a.walls_only = DVBE_WALLS_PATH;
   for (int q = 0; q < 4; ++q)
     for (const dvbe_bc_segment &g : pb.bc[q])
       if (g.kind != DVBE_BC_PERIODIC && g.kind != DVBE_BC_WALL_BOUNCEBACK && g.kind != DVBE_BC_WALL_DIFFUSE)

@@ -25,6 +25,12 @@ enum Scheme { SC_DUGKS = 0, SC_BKG_FV = 1, SC_BKG_FD = 2, SC_CFREE = 3 };
 #define DVBE_HALO 1
 #endif
 
+// Boundary strips of meshes whose non-periodic sides are all walls: 1 = the
+// general path compiled with the wall rules alone, 0 = with every rule.
+#ifndef DVBE_WALLS_PATH
+#define DVBE_WALLS_PATH 1
+#endif
+
 // Strip geometry.  A warp's lanes hold lane_cols adjacent columns each (two
 // for FP32 arithmetic, which then issues paired FP32 instructions; one for
 // FP64); NC halo columns on each side leave strip_cols output columns per
