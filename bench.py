@@ -571,6 +571,19 @@ def main():
         }
         if not a.no_cpu:
             line["cpu_baseline"] = cpu_baseline(a.scheme)
+        other = "bkg" if a.scheme == "dugks" else "dugks"
+        if f"{other}_{a.precision}" in extras:
+            # cost of a DUGKS step over a BKG step, here and in the paper (context only)
+            mlups = {a.scheme: value / world, other: extras[f"{other}_{a.precision}"]["MLUPS"]}
+            ratio = {"gpu": mlups["bkg"] / mlups["dugks"],
+                     "gpu_case": f"{a.n}^2 Taylor-Green, {a.precision} storage, one GB300",
+                     "paper": 1.88, "paper_case": "64^2 Taylor-Green, CPU code on an Intel Xeon "
+                                                  "E5-2670v3 at 2.6 GHz (Sec 3.1)"}
+            if not a.no_cpu:
+                c_d, t_d = _oracle_sample("dugks", 256, 4.0)
+                c_b, t_b = _oracle_sample("bkg", 256, 4.0)
+                ratio["oracle_1_thread"] = (c_b / t_b) / (c_d / t_d)
+            line["dugks_bkg_cost_ratio"] = ratio
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
