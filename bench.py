@@ -535,6 +535,9 @@ def main():
         extras["quad_wavy_1024_dugks_f64_multipass"] = dict(case_throughput(
             dv, stream, torch, cq, flq, "f64", 40, peak),
             note="six kernels per step with face arrays; hbm_frac against the 144 B/cell minimum")
+        extras["quad_wavy_1024_dugks_f32_multipass"] = dict(case_throughput(
+            dv, stream, torch, cq, flq, "f32", 40, peak),
+            note="FP32 storage and arithmetic; hbm_frac against the 72 B/cell minimum")
         ct, flt = workload(1024, "dugks")
         extras["tensor_1024_dugks_f64_multipass"] = case_throughput(
             dv, stream, torch, ct, flt, "f64", 40, peak, path="multipass")

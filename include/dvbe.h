@@ -134,14 +134,16 @@ typedef struct {
  * C's value carried to the foot point with C's central-difference gradient,
  * phi_C + (x_b - h xi - x_C) . grad phi_C; directions along a face, and faces
  * on non-periodic sides, keep the linear one.  It runs on the multi-pass
- * path (FP64), single solver only. */
+ * path (DVBE_F64 or DVBE_F32 storage), single solver only. */
 typedef enum { DVBE_RECON_LINEAR = 0, DVBE_RECON_UPWIND_CELL = 1 } dvbe_recon;
 
 /* Step implementation.  DVBE_PATH_FUSED: one fused kernel (two on meshes
  * with inner strips) per step, every precision.  DVBE_PATH_MULTIPASS: the
  * step as separate kernels with face arrays in device memory (cell stage,
  * ghost layers, x faces, y faces, update; about five times the memory traffic
- * of the fused step), FP64 only; it carries the reconstruction variants. */
+ * of the fused step), in FP64 or FP32 storage with arithmetic of the same
+ * precision (other storage modes: DVBE_ERR_UNSUPPORTED); it carries the
+ * reconstruction variants and the quadrilateral meshes. */
 typedef enum { DVBE_PATH_FUSED = 0, DVBE_PATH_MULTIPASS = 1 } dvbe_path;
 
 /* ---- velocity set and mesh --------------------------------------------- */
@@ -186,9 +188,9 @@ DVBE_API dvbe_status dvbe_mesh_geometry(dvbe_mesh mesh, double *xc, double *yc, 
  *     midpoint's y (W, E) or x (S, N); a periodic pair of sides must be
  *     translates of each other.
  * A tensor mesh given this way steps as dvbe_mesh_create's up to rounding.
- * Solvers on a quadrilateral mesh run the multi-pass FP64 step
- * (DVBE_PATH_MULTIPASS, DVBE_F64; otherwise DVBE_ERR_UNSUPPORTED); batches
- * take tensor meshes only. */
+ * Solvers on a quadrilateral mesh run the multi-pass step
+ * (DVBE_PATH_MULTIPASS; DVBE_F64 or DVBE_F32 storage, otherwise
+ * DVBE_ERR_UNSUPPORTED); batches take tensor meshes only. */
 DVBE_API dvbe_status dvbe_mesh_create_quad(int nx, int ny, const double *X, const double *Y,
                                            dvbe_mesh *out);
 /* Cell centres and volumes of either kind of mesh, each [ny][nx] (any may be

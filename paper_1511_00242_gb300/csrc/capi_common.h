@@ -76,26 +76,27 @@ struct DeviceProblem {
   double *volx = nullptr, *voly = nullptr;
 };
 
-// Buffers and tables of the multi-pass FP64 step (multipass.cu).
+// Buffers and tables of the multi-pass step (multipass.cu), all of one
+// element type: double (FP64 storage) or float (FP32 storage), elem bytes.
 struct MPArgs {
-  double *phi;         // [9][ny+4][nx+4]: phi with two ghost layers
+  void *phi;           // [9][ny+4][nx+4]: phi with two ghost layers
   long long pplane;    // (ny+4)(nx+4)
-  double *tp;          // [9][ny][nx]: f_tilde^+
-  double *fx, *fy;     // [9][ny][nx+1], [9][ny+1][nx]: face distributions
-  const double *xg;    // [nx+4]: cell c at c+2: h c / (x_{c+1} - x_{c-1})
-  const double *yg;    // [ny+4]
-  const double *xoff;  // [2(nx+1)]: face k: (x_b - x_{k-1}) / (h c), (x_b - x_k) / (h c)
-  const double *yoff;  // [2(ny+1)]
+  void *tp;            // [9][ny][nx]: f_tilde^+
+  void *fx, *fy;       // [9][ny][nx+1], [9][ny+1][nx]: face distributions
+  const void *xg;      // [nx+4]: cell c at c+2: h c / (x_{c+1} - x_{c-1})
+  const void *yg;      // [ny+4]
+  const void *xoff;    // [2(nx+1)]: face k: (x_b - x_{k-1}) / (h c), (x_b - x_k) / (h c)
+  const void *yoff;    // [2(ny+1)]
   double b_tp;         // f_tilde^+ = f_tilde + b_tp (f_eq - f_tilde)
-  int nx, ny, recon, scheme;
+  int nx, ny, recon, scheme, elem;
   // quadrilateral mesh (QuadHost on the device); quad == 0 on tensor meshes
   int quad;
   double eshift;
-  const double *jinv, *qfx, *qfy, *vs, *qext, *qbn;
+  const void *jinv, *qfx, *qfy, *vs, *qext, *qbn;
   const unsigned char *qmir;
 };
 // Tables of a quadrilateral mesh: validates it against the boundary
-// segments and fills pb.q, pb.segid and the CFL number.
+// segments and fills pb.q and pb.segid.
 dvbe_status quad_tables(const dvbe_mesh_ &m, Problem &pb);
 double quad_min_edge(const dvbe_mesh_ &m); // shortest cell edge
 cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s);

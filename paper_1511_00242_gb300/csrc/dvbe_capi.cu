@@ -184,12 +184,12 @@ dvbe_status build_problem(const dvbe_params *p, Problem &pb, bool halo) {
     return fail(DVBE_ERR_INVALID_ARG, "unknown step path");
   pb.recon = p->recon;
   pb.multipass = p->path == DVBE_PATH_MULTIPASS || p->recon == DVBE_RECON_UPWIND_CELL || m.quad;
-  if (m.quad && (p->precision != DVBE_F64 || p->bkg_fd))
-    return fail(DVBE_ERR_UNSUPPORTED, "a quadrilateral mesh runs the multi-pass step, in FP64 "
-                                      "and finite-volume form only");
-  if (pb.multipass && (p->precision != DVBE_F64 || p->bkg_fd))
+  if (m.quad && ((p->precision != DVBE_F64 && p->precision != DVBE_F32) || p->bkg_fd))
+    return fail(DVBE_ERR_UNSUPPORTED, "a quadrilateral mesh runs the multi-pass step, in FP64 or "
+                                      "FP32 storage and finite-volume form only");
+  if (pb.multipass && ((p->precision != DVBE_F64 && p->precision != DVBE_F32) || p->bkg_fd))
     return fail(DVBE_ERR_UNSUPPORTED, "the multi-pass step (and the upwind-cell reconstruction) runs "
-                                      "in FP64 and finite-volume form only");
+                                      "in FP64 or FP32 storage and finite-volume form only");
   if (pb.recon == DVBE_RECON_UPWIND_CELL && p->scheme == DVBE_CFREE_CENTRAL)
     return fail(DVBE_ERR_UNSUPPORTED, "the central collision-free face has no upwind-cell form");
   if (p->bkg_fd) {
@@ -603,61 +603,71 @@ struct dvbe_solver_ {
   CUtensorMap tm[2][2]; // [buffer][main, wrap]
 };
 
-// Buffers and tables of the multi-pass step in one device allocation.
+// Buffers and tables of the multi-pass step in one device allocation, in
+// the storage's element type (the cell volumes of a quadrilateral mesh stay
+// FP64, for the conserved sums).
 static dvbe_status alloc_multipass(dvbe_solver s) {
   const Problem &pb = s->pb;
   const long long nx = pb.nx, ny = pb.ny;
   const long long pplane = (nx + 4) * (ny + 4);
+  const size_t es = (size_t)pb.elem;
   // buffers, the tensor tables, then the quadrilateral-mesh tables (empty
-  // on tensor meshes); the mirror flags (bytes) last
+  // on tensor meshes); the FP64 volumes and the mirror flags (bytes) last
   const QuadHost &qh = pb.q;
-  const std::vector<double> *tab[11] = {&pb.xg, &pb.yg, &pb.xoff, &pb.yoff, &qh.jinv, &qh.fx,
-                                        &qh.fy, &qh.vs, &qh.vol, &qh.ext, &qh.bn};
-  long long counts[16] = {9 * pplane, 9 * nx * ny, 9 * (nx + 1) * ny, 9 * nx * (ny + 1)};
-  for (int q = 0; q < 11; ++q) counts[4 + q] = (long long)tab[q]->size();
+  const std::vector<double> *tab[10] = {&pb.xg, &pb.yg, &pb.xoff, &pb.yoff, &qh.jinv,
+                                        &qh.fx, &qh.fy, &qh.vs, &qh.ext, &qh.bn};
+  size_t bytes[16] = {es * 9 * pplane, es * 9 * nx * ny, es * 9 * (nx + 1) * ny, es * 9 * nx * (ny + 1)};
+  for (int q = 0; q < 10; ++q) bytes[4 + q] = es * tab[q]->size();
+  bytes[14] = sizeof(double) * qh.vol.size();
+  bytes[15] = qh.mir.size();
   size_t off[16], total = 0;
-  for (int q = 0; q < 15; ++q) {
+  for (int q = 0; q < 16; ++q) {
     off[q] = total;
-    total += ((size_t)counts[q] * sizeof(double) + 255) / 256 * 256;
+    total += (bytes[q] + 255) / 256 * 256;
   }
-  off[15] = total;
-  total += (qh.mir.size() + 255) / 256 * 256;
   s->mpblob = (char *)dmalloc(total, s->stream);
   if (!s->mpblob) return fail(DVBE_ERR_OOM, "device allocation of the multi-pass buffers failed");
-  cudaError_t e = cudaMemsetAsync(s->mpblob, 0, total, s->stream);
-  for (int q = 0; q < 11 && e == cudaSuccess; ++q)
-    if (!tab[q]->empty())
-      e = cudaMemcpyAsync(s->mpblob + off[4 + q], tab[q]->data(), sizeof(double) * tab[q]->size(),
-                          cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess && !qh.mir.empty())
-    e = cudaMemcpyAsync(s->mpblob + off[15], qh.mir.data(), qh.mir.size(), cudaMemcpyHostToDevice,
-                        s->stream);
+  std::vector<char> host(total - off[4], 0);
+  for (int q = 0; q < 10; ++q) {
+    char *dst = host.data() + (off[4 + q] - off[4]);
+    const std::vector<double> &v = *tab[q];
+    if (es == 8)
+      memcpy(dst, v.data(), sizeof(double) * v.size());
+    else
+      for (size_t k = 0; k < v.size(); ++k) ((float *)dst)[k] = (float)v[k];
+  }
+  if (!qh.vol.empty()) memcpy(host.data() + (off[14] - off[4]), qh.vol.data(), bytes[14]);
+  if (!qh.mir.empty()) memcpy(host.data() + (off[15] - off[4]), qh.mir.data(), bytes[15]);
+  cudaError_t e = cudaMemsetAsync(s->mpblob, 0, off[4], s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->mpblob + off[4], host.data(), host.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "multi-pass set-up");
   MPArgs &m = s->mp;
-  m.phi = (double *)(s->mpblob + off[0]);
+  m.phi = s->mpblob + off[0];
   m.pplane = pplane;
-  m.tp = (double *)(s->mpblob + off[1]);
-  m.fx = (double *)(s->mpblob + off[2]);
-  m.fy = (double *)(s->mpblob + off[3]);
-  m.xg = (const double *)(s->mpblob + off[4]);
-  m.yg = (const double *)(s->mpblob + off[5]);
-  m.xoff = (const double *)(s->mpblob + off[6]);
-  m.yoff = (const double *)(s->mpblob + off[7]);
+  m.tp = s->mpblob + off[1];
+  m.fx = s->mpblob + off[2];
+  m.fy = s->mpblob + off[3];
+  m.xg = s->mpblob + off[4];
+  m.yg = s->mpblob + off[5];
+  m.xoff = s->mpblob + off[6];
+  m.yoff = s->mpblob + off[7];
   m.b_tp = pb.b_tp;
   m.nx = pb.nx;
   m.ny = pb.ny;
   m.recon = pb.recon;
   m.scheme = pb.kernel;
+  m.elem = pb.elem;
   m.quad = pb.quad ? 1 : 0;
   m.eshift = qh.eshift;
-  m.jinv = (const double *)(s->mpblob + off[8]);
-  m.qfx = (const double *)(s->mpblob + off[9]);
-  m.qfy = (const double *)(s->mpblob + off[10]);
-  m.vs = (const double *)(s->mpblob + off[11]);
-  s->qvol = (const double *)(s->mpblob + off[12]);
-  m.qext = (const double *)(s->mpblob + off[13]);
-  m.qbn = (const double *)(s->mpblob + off[14]);
+  m.jinv = s->mpblob + off[8];
+  m.qfx = s->mpblob + off[9];
+  m.qfy = s->mpblob + off[10];
+  m.vs = s->mpblob + off[11];
+  m.qext = s->mpblob + off[12];
+  m.qbn = s->mpblob + off[13];
+  s->qvol = (const double *)(s->mpblob + off[14]);
   m.qmir = (const unsigned char *)(s->mpblob + off[15]);
   return DVBE_OK;
 }

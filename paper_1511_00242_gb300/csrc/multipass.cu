@@ -16,8 +16,11 @@
 //      and back-transform to f (Sec 2.2);
 //   5. update f_tilde^{n+1} = f_tilde^+ - dt/|V| sum (xi . n) A f_face.
 //
-// Everything is FP64 on f_tilde itself; the geometry tables are those of
-// the fused kernel (CaseArgs) plus the foot offsets of the upwind cells.
+// The arithmetic is on f_tilde itself, in the storage's precision: FP64, or
+// FP32 (absolute storage; the equilibrium then takes the exact-sum weights
+// of EqCoef, so the collision keeps mass and momentum up to unbiased
+// rounding).  The geometry tables are those of the fused kernel (CaseArgs)
+// plus the foot offsets of the upwind cells, all in that precision.
 // Quadrilateral meshes run the same stages with their own ghost, face and
 // update kernels (tables of quad_mesh.cu).
 #include "capi_common.h"
@@ -37,53 +40,64 @@ __device__ __forceinline__ long long pidx(const MPArgs &m, int i, int j) {
   return (long long)(j + 2) * (m.nx + 4) + (i + 2);
 }
 
-__device__ __forceinline__ void feq9(double rho, double Ux, double Uy, double *f) {
+// Equilibrium weights in the arithmetic's precision: FP64 the rounded 4/9,
+// 1/9, 1/36; FP32 the exact-sum weights of EqCoef (their sum is 1 in FP32).
+template <typename R> __device__ __forceinline__ R wgt(int a);
+template <> __device__ __forceinline__ double wgt<double>(int a) { return WGT(a); }
+template <> __device__ __forceinline__ float wgt<float>(int a) {
+  using C = dev::EqCoef<float>;
+  return a == 0 ? C::W0 : (a <= 4 ? C::W1 : C::W2);
+}
+
+template <typename R> __device__ __forceinline__ void feq9(R rho, R Ux, R Uy, R *f) {
   // Eq. equilibrium with U = u / c: w rho (1 + 3 e.U + 4.5 (e.U)^2 - 1.5 |U|^2)
-  const double u2 = Ux * Ux + Uy * Uy;
+  const R u2 = Ux * Ux + Uy * Uy;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const double eu = EX(a) * Ux + EY(a) * Uy;
-    f[a] = WGT(a) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * u2);
+    const R eu = R(EX(a)) * Ux + R(EY(a)) * Uy;
+    f[a] = wgt<R>(a) * rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * u2);
   }
 }
 
-__device__ __forceinline__ void mom9(const double *f, double &rho, double &Ux, double &Uy) {
-  double r = 0, mx = 0, my = 0;
+template <typename R> __device__ __forceinline__ void mom9(const R *f, R &rho, R &Ux, R &Uy) {
+  R r = 0, mx = 0, my = 0;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     r += f[a];
-    mx += EX(a) * f[a];
-    my += EY(a) * f[a];
+    mx += R(EX(a)) * f[a];
+    my += R(EY(a)) * f[a];
   }
   rho = r;
   Ux = mx / r;
   Uy = my / r;
 }
 
-__global__ void k_stage(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_stage(CaseArgs A, MPArgs m) {
   const long long n = (long long)A.nx * A.ny;
-  const double *f = (const double *)A.fin;
+  const R *f = (const R *)A.fin;
+  R *phi = (R *)m.phi, *tp = (R *)m.tp;
+  const R bphi = R(A.b_phi), btp = R(m.b_tp);
   for (long long k = blockIdx.x * (long long)T + threadIdx.x; k < n; k += (long long)gridDim.x * T) {
     const int j = (int)(k / A.nx), i = (int)(k % A.nx);
     const long long idx = (long long)j * A.pitch + i;
-    double d[9], fe[9], rho, Ux, Uy;
+    R d[9], fe[9], rho, Ux, Uy;
 #pragma unroll
     for (int a = 0; a < 9; ++a) d[a] = f[a * A.plane + idx];
     mom9(d, rho, Ux, Uy);
-    if (!(rho > 0 && rho < 1e30)) atomicOr(A.flag, 1u);
+    if (!(rho > R(0) && rho < R(1e30))) atomicOr(A.flag, 1u);
     feq9(rho, Ux, Uy, fe);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      m.phi[a * m.pplane + pidx(m, i, j)] = d[a] + A.b_phi * (fe[a] - d[a]);
-      m.tp[a * n + k] = d[a] + m.b_tp * (fe[a] - d[a]);
+      phi[a * m.pplane + pidx(m, i, j)] = d[a] + bphi * (fe[a] - d[a]);
+      tp[a * n + k] = d[a] + btp * (fe[a] - d[a]);
     }
   }
 }
 
-__global__ void k_ghost_x(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_ghost_x(CaseArgs A, MPArgs m) {
   const int j = blockIdx.x * T + threadIdx.x;
   if (j >= A.ny) return;
-  double *P = m.phi;
+  R *P = (R *)m.phi;
   for (int side = 0; side < 2; ++side) {
     if (A.per_x) {
       for (int l = 1; l <= 2; ++l) {
@@ -93,21 +107,21 @@ __global__ void k_ghost_x(CaseArgs A, MPArgs m) {
       continue;
     }
     const int ig = side == 0 ? -1 : A.nx, i1 = side == 0 ? 0 : A.nx - 1, i2 = side == 0 ? 1 : A.nx - 2;
-    double p1[9], p2[9], g[9];
+    R p1[9], p2[9], g[9];
     for (int a = 0; a < 9; ++a) {
       p1[a] = P[a * m.pplane + pidx(m, i1, j)];
       p2[a] = P[a * m.pplane + pidx(m, i2, j)];
-      g[a] = 0.0;
+      g[a] = R(0);
     }
-    dev::apply_ghost<double, true>(A.seg[side][A.segid[side][j]], A.ext[side], 0.0, p1, p2, g);
+    dev::apply_ghost<R, true>(A.seg[side][A.segid[side][j]], R(A.ext[side]), R(0), p1, p2, g);
     for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, ig, j)] = g[a];
   }
 }
 
-__global__ void k_ghost_y(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_ghost_y(CaseArgs A, MPArgs m) {
   const int i = blockIdx.x * T + threadIdx.x - 2; // -2 .. nx+1
   if (i > A.nx + 1) return;
-  double *P = m.phi;
+  R *P = (R *)m.phi;
   const int ic = min(max(i, 0), A.nx - 1);
   for (int side = 2; side < 4; ++side) {
     if (A.per_y) {
@@ -118,114 +132,118 @@ __global__ void k_ghost_y(CaseArgs A, MPArgs m) {
       continue;
     }
     const int jg = side == 2 ? -1 : A.ny, j1 = side == 2 ? 0 : A.ny - 1, j2 = side == 2 ? 1 : A.ny - 2;
-    double p1[9], p2[9], g[9];
+    R p1[9], p2[9], g[9];
     for (int a = 0; a < 9; ++a) {
       p1[a] = P[a * m.pplane + pidx(m, i, j1)];
       p2[a] = P[a * m.pplane + pidx(m, i, j2)];
-      g[a] = 0.0;
+      g[a] = R(0);
     }
-    dev::apply_ghost<double, false>(A.seg[side][A.segid[side][ic]], A.ext[side], 0.0, p1, p2, g);
+    dev::apply_ghost<R, false>(A.seg[side][A.segid[side][ic]], R(A.ext[side]), R(0), p1, p2, g);
     for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, i, jg)] = g[a];
   }
 }
 
 // DUGKS face moments and back-transform f = f_bar + q (f_eq - f_bar).
-__device__ __forceinline__ void dugks_back(const CaseArgs &A, double *F) {
-  double rho, Ux, Uy, fe[9];
+template <typename R> __device__ __forceinline__ void dugks_back(const CaseArgs &A, R *F) {
+  R rho, Ux, Uy, fe[9];
   mom9(F, rho, Ux, Uy);
   feq9(rho, Ux, Uy, fe);
+  const R q = R(A.q_face);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) F[a] += A.q_face * (fe[a] - F[a]);
+  for (int a = 0; a < 9; ++a) F[a] += q * (fe[a] - F[a]);
 }
 
 // x-face k between cells k-1 and k, row j.  Tables: xfth[k+1] theta and
 // xfs[k+1] = h c / (x_k - x_{k-1}) (CaseArgs, FP64); m.xg[c+2] = h c /
 // (x_{c+1} - x_{c-1}) for cells c = -2 .. nx+1 (m.yg likewise); m.xoff[2k],
 // [2k+1] = (x_b - x_C) / (h c) for C = k-1 and C = k.
-__global__ void k_faces_x(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_faces_x(CaseArgs A, MPArgs m) {
   const long long n = (long long)(A.nx + 1) * A.ny;
-  const double *xfth = (const double *)A.xfth, *xfs = (const double *)A.xfs;
-  const double *P = m.phi;
+  const R *xfth = (const R *)A.xfth, *xfs = (const R *)A.xfs;
+  const R *P = (const R *)m.phi;
+  const R *xg = (const R *)m.xg, *yg = (const R *)m.yg, *xoff = (const R *)m.xoff;
   for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
     const int j = (int)(t / (A.nx + 1)), k = (int)(t % (A.nx + 1));
-    const double th = xfth[k + 1], s = xfs[k + 1], ty = m.yg[j + 2];
+    const R th = xfth[k + 1], s = xfs[k + 1], ty = yg[j + 2];
     const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_x || (k > 0 && k < A.nx));
-    double F[9];
+    R F[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const double *Pa = P + a * m.pplane;
+      const R *Pa = P + a * m.pplane;
       if (upw && EX(a) != 0) {
         const int C = EX(a) > 0 ? k - 1 : k;
-        const double gx = (Pa[pidx(m, C + 1, j)] - Pa[pidx(m, C - 1, j)]) * m.xg[C + 2];
-        const double gy = (Pa[pidx(m, C, j + 1)] - Pa[pidx(m, C, j - 1)]) * ty;
-        const double off = m.xoff[2 * k + (EX(a) > 0 ? 0 : 1)];
-        F[a] = Pa[pidx(m, C, j)] + (off - EX(a)) * gx - EY(a) * gy;
+        const R gx = (Pa[pidx(m, C + 1, j)] - Pa[pidx(m, C - 1, j)]) * xg[C + 2];
+        const R gy = (Pa[pidx(m, C, j + 1)] - Pa[pidx(m, C, j - 1)]) * ty;
+        const R off = xoff[2 * k + (EX(a) > 0 ? 0 : 1)];
+        F[a] = Pa[pidx(m, C, j)] + (off - R(EX(a))) * gx - R(EY(a)) * gy;
         continue;
       }
-      const double pl = Pa[pidx(m, k - 1, j)], pr = Pa[pidx(m, k, j)];
-      const double gl = (Pa[pidx(m, k - 1, j + 1)] - Pa[pidx(m, k - 1, j - 1)]) * ty;
-      const double gr = (Pa[pidx(m, k, j + 1)] - Pa[pidx(m, k, j - 1)]) * ty;
-      F[a] = (1.0 - th) * pl + th * pr - EX(a) * s * (pr - pl) - EY(a) * ((1.0 - th) * gl + th * gr);
+      const R pl = Pa[pidx(m, k - 1, j)], pr = Pa[pidx(m, k, j)];
+      const R gl = (Pa[pidx(m, k - 1, j + 1)] - Pa[pidx(m, k - 1, j - 1)]) * ty;
+      const R gr = (Pa[pidx(m, k, j + 1)] - Pa[pidx(m, k, j - 1)]) * ty;
+      F[a] = (R(1) - th) * pl + th * pr - R(EX(a)) * s * (pr - pl) - R(EY(a)) * ((R(1) - th) * gl + th * gr);
     }
     if (!A.per_x && (k == 0 || k == A.nx)) {
       const int side = k == 0 ? 0 : 1;
-      dev::face_bc<double>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, 0.0, F);
+      dev::face_bc<R>(A.seg[side][A.segid[side][j]], side == 0 ? -1 : 1, 0, R(0), F);
     }
     if (m.scheme == SC_DUGKS) dugks_back(A, F);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) m.fx[a * n + t] = F[a];
+    for (int a = 0; a < 9; ++a) ((R *)m.fx)[a * n + t] = F[a];
   }
 }
 
-__global__ void k_faces_y(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_faces_y(CaseArgs A, MPArgs m) {
   const long long n = (long long)A.nx * (A.ny + 1);
-  const double *yfth = (const double *)A.yfth, *yfs = (const double *)A.yfs;
-  const double *P = m.phi;
+  const R *yfth = (const R *)A.yfth, *yfs = (const R *)A.yfs;
+  const R *P = (const R *)m.phi;
+  const R *xg = (const R *)m.xg, *yg = (const R *)m.yg, *yoff = (const R *)m.yoff;
   for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
     const int k = (int)(t / A.nx), i = (int)(t % A.nx);
-    const double th = yfth[k + 1], s = yfs[k + 1], tx = m.xg[i + 2];
+    const R th = yfth[k + 1], s = yfs[k + 1], tx = xg[i + 2];
     const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_y || (k > 0 && k < A.ny));
-    double F[9];
+    R F[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const double *Pa = P + a * m.pplane;
+      const R *Pa = P + a * m.pplane;
       if (upw && EY(a) != 0) {
         const int C = EY(a) > 0 ? k - 1 : k;
-        const double gy = (Pa[pidx(m, i, C + 1)] - Pa[pidx(m, i, C - 1)]) * m.yg[C + 2];
-        const double gx = (Pa[pidx(m, i + 1, C)] - Pa[pidx(m, i - 1, C)]) * tx;
-        const double off = m.yoff[2 * k + (EY(a) > 0 ? 0 : 1)];
-        F[a] = Pa[pidx(m, i, C)] + (off - EY(a)) * gy - EX(a) * gx;
+        const R gy = (Pa[pidx(m, i, C + 1)] - Pa[pidx(m, i, C - 1)]) * yg[C + 2];
+        const R gx = (Pa[pidx(m, i + 1, C)] - Pa[pidx(m, i - 1, C)]) * tx;
+        const R off = yoff[2 * k + (EY(a) > 0 ? 0 : 1)];
+        F[a] = Pa[pidx(m, i, C)] + (off - R(EY(a))) * gy - R(EX(a)) * gx;
         continue;
       }
-      const double pl = Pa[pidx(m, i, k - 1)], pr = Pa[pidx(m, i, k)];
-      const double gl = (Pa[pidx(m, i + 1, k - 1)] - Pa[pidx(m, i - 1, k - 1)]) * tx;
-      const double gr = (Pa[pidx(m, i + 1, k)] - Pa[pidx(m, i - 1, k)]) * tx;
-      F[a] = (1.0 - th) * pl + th * pr - EY(a) * s * (pr - pl) - EX(a) * ((1.0 - th) * gl + th * gr);
+      const R pl = Pa[pidx(m, i, k - 1)], pr = Pa[pidx(m, i, k)];
+      const R gl = (Pa[pidx(m, i + 1, k - 1)] - Pa[pidx(m, i - 1, k - 1)]) * tx;
+      const R gr = (Pa[pidx(m, i + 1, k)] - Pa[pidx(m, i - 1, k)]) * tx;
+      F[a] = (R(1) - th) * pl + th * pr - R(EY(a)) * s * (pr - pl) - R(EX(a)) * ((R(1) - th) * gl + th * gr);
     }
     if (!A.per_y && (k == 0 || k == A.ny)) {
       const int side = k == 0 ? 2 : 3;
-      dev::face_bc<double>(A.seg[side][A.segid[side][i]], 0, side == 2 ? -1 : 1, 0.0, F);
+      dev::face_bc<R>(A.seg[side][A.segid[side][i]], 0, side == 2 ? -1 : 1, R(0), F);
     }
     if (m.scheme == SC_DUGKS) dugks_back(A, F);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) m.fy[a * n + t] = F[a];
+    for (int a = 0; a < 9; ++a) ((R *)m.fy)[a * n + t] = F[a];
   }
 }
 
-__global__ void k_update(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_update(CaseArgs A, MPArgs m) {
   const long long n = (long long)A.nx * A.ny;
   const long long nfx = (long long)(A.nx + 1) * A.ny, nfy = (long long)A.nx * (A.ny + 1);
-  const double *xcu = (const double *)A.xcu, *ycu = (const double *)A.ycu;
-  double *fo = (double *)A.fout;
+  const R *xcu = (const R *)A.xcu, *ycu = (const R *)A.ycu;
+  const R *tp = (const R *)m.tp, *fx = (const R *)m.fx, *fy = (const R *)m.fy;
+  R *fo = (R *)A.fout;
   for (long long k = blockIdx.x * (long long)T + threadIdx.x; k < n; k += (long long)gridDim.x * T) {
     const int j = (int)(k / A.nx), i = (int)(k % A.nx);
-    const double cx = xcu[i + 1], cy = ycu[j + 1];
+    const R cx = xcu[i + 1], cy = ycu[j + 1];
     const long long w = (long long)j * (A.nx + 1) + i, s = (long long)j * A.nx + i;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      double v = m.tp[a * n + k];
-      if (EX(a) != 0) v -= cx * EX(a) * (m.fx[a * nfx + w + 1] - m.fx[a * nfx + w]);
-      if (EY(a) != 0) v -= cy * EY(a) * (m.fy[a * nfy + s + A.nx] - m.fy[a * nfy + s]);
+      R v = tp[a * n + k];
+      if (EX(a) != 0) v -= cx * R(EX(a)) * (fx[a * nfx + w + 1] - fx[a * nfx + w]);
+      if (EY(a) != 0) v -= cy * R(EY(a)) * (fy[a * nfy + s + A.nx] - fy[a * nfy + s]);
       fo[a * A.plane + (long long)j * A.pitch + i] = v;
     }
   }
@@ -245,52 +263,56 @@ __global__ void k_update(CaseArgs A, MPArgs m) {
 
 // s grad phi at padded cell (i, j): central differences along the mesh
 // lines, one-sided at the outer ghost layer of a side that is not periodic.
-__device__ __forceinline__ void qgrad(const CaseArgs &A, const MPArgs &m, const double *Pa, int i,
-                                      int j, double &gx, double &gy) {
+template <typename R>
+__device__ __forceinline__ void qgrad(const CaseArgs &A, const MPArgs &m, const R *Pa, int i, int j,
+                                      R &gx, R &gy) {
   const int im = (!A.per_x && i <= -1) ? i : i - 1, ip = (!A.per_x && i >= A.nx) ? i : i + 1;
   const int jm = (!A.per_y && j <= -1) ? j : j - 1, jp = (!A.per_y && j >= A.ny) ? j : j + 1;
-  const double di = Pa[pidx(m, ip, j)] - Pa[pidx(m, im, j)];
-  const double dj = Pa[pidx(m, i, jp)] - Pa[pidx(m, i, jm)];
+  const R di = Pa[pidx(m, ip, j)] - Pa[pidx(m, im, j)];
+  const R dj = Pa[pidx(m, i, jp)] - Pa[pidx(m, i, jm)];
   const long long c = pidx(m, i, j);
-  gx = m.jinv[c] * di + m.jinv[m.pplane + c] * dj;
-  gy = m.jinv[2 * m.pplane + c] * di + m.jinv[3 * m.pplane + c] * dj;
+  const R *J = (const R *)m.jinv;
+  gx = J[c] * di + J[m.pplane + c] * dj;
+  gy = J[2 * m.pplane + c] * di + J[3 * m.pplane + c] * dj;
 }
 
 // Sec 2.5 at a boundary face with outward normal (nxo, nyo) of any
-// orientation: full f (FP64).  Only directions crossing the face change.
-__device__ __forceinline__ void qface_bc(const SegParam &sp, double nxo, double nyo, double (&F)[9]) {
+// orientation, on full f.  Only directions crossing the face change.
+template <typename R> __device__ __forceinline__ void qface_bc(const SegParam &sp, R nxo, R nyo, R (&F)[9]) {
   if (sp.kind == DVBE_BC_WALL_BOUNCEBACK) {
+    const R ux = R(sp.ux), uy = R(sp.uy);
 #pragma unroll
     for (int a = 1; a < 9; ++a)
-      if (EX(a) * nxo + EY(a) * nyo > 0)
-        F[dev::OPP(a)] = F[a] - 6.0 * WGT(a) * (EX(a) * sp.ux + EY(a) * sp.uy);
+      if (R(EX(a)) * nxo + R(EY(a)) * nyo > R(0))
+        F[dev::OPP(a)] = F[a] - R(6.0 * WGT(a)) * (R(EX(a)) * ux + R(EY(a)) * uy);
   } else if (sp.kind == DVBE_BC_WALL_DIFFUSE) {
-    double f1[9];
-    feq9(1.0, sp.ux, sp.uy, f1);
-    double num = 0, den = 0;
+    R f1[9];
+    feq9(R(1), R(sp.ux), R(sp.uy), f1);
+    R num = 0, den = 0;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-      const double en = EX(a) * nxo + EY(a) * nyo;
-      if (en > 0) num += en * F[a];
-      if (en < 0) den -= en * f1[a];
+      const R en = R(EX(a)) * nxo + R(EY(a)) * nyo;
+      if (en > R(0)) num += en * F[a];
+      if (en < R(0)) den -= en * f1[a];
     }
-    const double rw = num / den;
+    const R rw = num / den;
 #pragma unroll
     for (int a = 1; a < 9; ++a)
-      if (EX(a) * nxo + EY(a) * nyo < 0) F[a] = rw * f1[a];
+      if (R(EX(a)) * nxo + R(EY(a)) * nyo < R(0)) F[a] = rw * f1[a];
   } else if (sp.kind == DVBE_BC_INFLOW_EQ) {
-    double fe[9];
-    feq9(sp.rho, sp.ux, sp.uy, fe);
+    R fe[9];
+    feq9(R(sp.rho), R(sp.ux), R(sp.uy), fe);
 #pragma unroll
     for (int a = 1; a < 9; ++a)
-      if (EX(a) * nxo + EY(a) * nyo < 0) F[a] = fe[a];
+      if (R(EX(a)) * nxo + R(EY(a)) * nyo < R(0)) F[a] = fe[a];
   }
 }
 
-__global__ void k_qghost_x(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_qghost_x(CaseArgs A, MPArgs m) {
   const int j = blockIdx.x * T + threadIdx.x;
   if (j >= A.ny) return;
-  double *P = m.phi;
+  R *P = (R *)m.phi;
+  const R *ext = (const R *)m.qext;
   for (int side = 0; side < 2; ++side) {
     if (A.per_x) {
       for (int l = 1; l <= 2; ++l) {
@@ -300,27 +322,28 @@ __global__ void k_qghost_x(CaseArgs A, MPArgs m) {
       continue;
     }
     const int ig = side == 0 ? -1 : A.nx, i1 = side == 0 ? 0 : A.nx - 1, i2 = side == 0 ? 1 : A.nx - 2;
-    double p1[9], p2[9], g[9];
+    R p1[9], p2[9], g[9];
     for (int a = 0; a < 9; ++a) {
       p1[a] = P[a * m.pplane + pidx(m, i1, j)];
       p2[a] = P[a * m.pplane + pidx(m, i2, j)];
-      g[a] = 0.0;
+      g[a] = R(0);
     }
     const long long q = (long long)side * A.ny + j;
     const SegParam &sp = A.seg[side][A.segid[side][j]];
     if (m.qmir[q])
-      dev::apply_ghost<double, true>(sp, m.qext[q], 0.0, p1, p2, g);
+      dev::apply_ghost<R, true>(sp, ext[q], R(0), p1, p2, g);
     else
-      dev::apply_ghost<double, false>(sp, m.qext[q], 0.0, p1, p2, g);
+      dev::apply_ghost<R, false>(sp, ext[q], R(0), p1, p2, g);
     for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, ig, j)] = g[a];
   }
 }
 
-__global__ void k_qghost_y(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_qghost_y(CaseArgs A, MPArgs m) {
   const int lo = A.per_x ? -2 : -1, hi = A.per_x ? A.nx + 1 : A.nx;
   const int i = blockIdx.x * T + threadIdx.x + lo;
   if (i > hi) return;
-  double *P = m.phi;
+  R *P = (R *)m.phi;
+  const R *ext = (const R *)m.qext;
   const int ic = min(max(i, 0), A.nx - 1);
   for (int side = 2; side < 4; ++side) {
     if (A.per_y) {
@@ -331,113 +354,121 @@ __global__ void k_qghost_y(CaseArgs A, MPArgs m) {
       continue;
     }
     const int jg = side == 2 ? -1 : A.ny, j1 = side == 2 ? 0 : A.ny - 1, j2 = side == 2 ? 1 : A.ny - 2;
-    double p1[9], p2[9], g[9];
+    R p1[9], p2[9], g[9];
     for (int a = 0; a < 9; ++a) {
       p1[a] = P[a * m.pplane + pidx(m, i, j1)];
       p2[a] = P[a * m.pplane + pidx(m, i, j2)];
-      g[a] = 0.0;
+      g[a] = R(0);
     }
     const long long q = 2LL * A.ny + (long long)(side - 2) * (A.nx + 4) + (i + 2);
     const SegParam &sp = A.seg[side][A.segid[side][ic]];
     if (m.qmir[q])
-      dev::apply_ghost<double, true>(sp, m.qext[q], 0.0, p1, p2, g);
+      dev::apply_ghost<R, true>(sp, ext[q], R(0), p1, p2, g);
     else
-      dev::apply_ghost<double, false>(sp, m.qext[q], 0.0, p1, p2, g);
+      dev::apply_ghost<R, false>(sp, ext[q], R(0), p1, p2, g);
     for (int a = 0; a < 9; ++a) P[a * m.pplane + pidx(m, i, jg)] = g[a];
   }
 }
 
 // One face between padded cells L = (iL, jL) and R = (iR, jR); tab[r * nf + f]
 // its tables.  Writes the nine face values phi(x_b - h xi).
-__device__ __forceinline__ void qface(const CaseArgs &A, const MPArgs &m, const double *tab,
-                                      long long nf, long long f, int iL, int jL, int iR, int jR,
-                                      bool upwind, double (&F)[9]) {
-  const double th = tab[QF_TH * nf + f], ox = tab[QF_OX * nf + f], oy = tab[QF_OY * nf + f];
-  const double dx = tab[QF_DX * nf + f], dy = tab[QF_DY * nf + f];
-  const double tx = tab[QF_TX * nf + f], ty = tab[QF_TY * nf + f];
-  const double bx = tab[QF_BX * nf + f], by = tab[QF_BY * nf + f];
-  const double nx = tab[QF_NX * nf + f], ny = tab[QF_NY * nf + f];
-  const long long L = pidx(m, iL, jL), R = pidx(m, iR, jR);
+template <typename R>
+__device__ __forceinline__ void qface(const CaseArgs &A, const MPArgs &m, const R *tab, long long nf,
+                                      long long f, int iL, int jL, int iR, int jR, bool upwind,
+                                      R (&F)[9]) {
+  const R th = tab[QF_TH * nf + f], ox = tab[QF_OX * nf + f], oy = tab[QF_OY * nf + f];
+  const R dx = tab[QF_DX * nf + f], dy = tab[QF_DY * nf + f];
+  const R tx = tab[QF_TX * nf + f], ty = tab[QF_TY * nf + f];
+  const R bx = tab[QF_BX * nf + f], by = tab[QF_BY * nf + f];
+  const R nx = tab[QF_NX * nf + f], ny = tab[QF_NY * nf + f];
+  const R es = R(m.eshift);
+  const long long cl = pidx(m, iL, jL), cr = pidx(m, iR, jR);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const double *Pa = m.phi + a * m.pplane;
-    const double en = EX(a) * nx + EY(a) * ny;
-    if (upwind && en != 0) {
-      double gx, gy;
-      if (en > 0) {
+    const R *Pa = (const R *)m.phi + a * m.pplane;
+    const R ex = R(EX(a)), ey = R(EY(a));
+    const R en = ex * nx + ey * ny;
+    if (upwind && en != R(0)) {
+      R gx, gy;
+      if (en > R(0)) {
         qgrad(A, m, Pa, iL, jL, gx, gy);
-        F[a] = Pa[L] + (bx - EX(a)) * gx + (by - EY(a)) * gy;
+        F[a] = Pa[cl] + (bx - ex) * gx + (by - ey) * gy;
       } else {
         qgrad(A, m, Pa, iR, jR, gx, gy);
-        F[a] = Pa[R] + (bx - dx - EX(a)) * gx + (by - dy - EY(a)) * gy;
+        F[a] = Pa[cr] + (bx - dx - ex) * gx + (by - dy - ey) * gy;
       }
       continue;
     }
-    double glx, gly, grx, gry;
+    R glx, gly, grx, gry;
     qgrad(A, m, Pa, iL, jL, glx, gly);
     qgrad(A, m, Pa, iR, jR, grx, gry);
-    const double gbx = (1.0 - th) * glx + th * grx, gby = (1.0 - th) * gly + th * gry;
-    const double pb = (1.0 - th) * Pa[L] + th * Pa[R] + gbx * ox + gby * oy;
-    const double corr = (Pa[R] - Pa[L]) - (gbx * dx + gby * dy);
-    const double gfx = gbx + corr * tx, gfy = gby + corr * ty;
-    F[a] = pb - m.eshift * (EX(a) * gfx + EY(a) * gfy);
+    const R gbx = (R(1) - th) * glx + th * grx, gby = (R(1) - th) * gly + th * gry;
+    const R pb = (R(1) - th) * Pa[cl] + th * Pa[cr] + gbx * ox + gby * oy;
+    const R corr = (Pa[cr] - Pa[cl]) - (gbx * dx + gby * dy);
+    const R gfx = gbx + corr * tx, gfy = gby + corr * ty;
+    F[a] = pb - es * (ex * gfx + ey * gfy);
   }
 }
 
-__global__ void k_qfaces_x(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_qfaces_x(CaseArgs A, MPArgs m) {
   const long long n = (long long)(A.nx + 1) * A.ny;
+  const R *bnt = (const R *)m.qbn;
   for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
     const int j = (int)(t / (A.nx + 1)), k = (int)(t % (A.nx + 1));
     const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_x || (k > 0 && k < A.nx));
-    double F[9];
-    qface(A, m, m.qfx, n, t, k - 1, j, k, j, upw, F);
+    R F[9];
+    qface(A, m, (const R *)m.qfx, n, t, k - 1, j, k, j, upw, F);
     if (!A.per_x && (k == 0 || k == A.nx)) {
       const int side = k == 0 ? 0 : 1;
-      const double *bn = m.qbn + (long long)side * 2 * A.ny + 2 * j;
+      const R *bn = bnt + (long long)side * 2 * A.ny + 2 * j;
       qface_bc(A.seg[side][A.segid[side][j]], bn[0], bn[1], F);
     }
     if (m.scheme == SC_DUGKS) dugks_back(A, F);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) m.fx[a * n + t] = F[a];
+    for (int a = 0; a < 9; ++a) ((R *)m.fx)[a * n + t] = F[a];
   }
 }
 
-__global__ void k_qfaces_y(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_qfaces_y(CaseArgs A, MPArgs m) {
   const long long n = (long long)A.nx * (A.ny + 1);
+  const R *bnt = (const R *)m.qbn;
   for (long long t = blockIdx.x * (long long)T + threadIdx.x; t < n; t += (long long)gridDim.x * T) {
     const int k = (int)(t / A.nx), i = (int)(t % A.nx);
     const bool upw = m.recon == DVBE_RECON_UPWIND_CELL && (A.per_y || (k > 0 && k < A.ny));
-    double F[9];
-    qface(A, m, m.qfy, n, t, i, k - 1, i, k, upw, F);
+    R F[9];
+    qface(A, m, (const R *)m.qfy, n, t, i, k - 1, i, k, upw, F);
     if (!A.per_y && (k == 0 || k == A.ny)) {
       const int side = k == 0 ? 2 : 3;
-      const double *bn = m.qbn + 4LL * A.ny + (long long)(side - 2) * 2 * A.nx + 2 * i;
+      const R *bn = bnt + 4LL * A.ny + (long long)(side - 2) * 2 * A.nx + 2 * i;
       qface_bc(A.seg[side][A.segid[side][i]], bn[0], bn[1], F);
     }
     if (m.scheme == SC_DUGKS) dugks_back(A, F);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) m.fy[a * n + t] = F[a];
+    for (int a = 0; a < 9; ++a) ((R *)m.fy)[a * n + t] = F[a];
   }
 }
 
 // f_tilde^{n+1} = f_tilde^+ - dt c / |V| sum over the faces of (e . n_out A) f_face
-__global__ void k_qupdate(CaseArgs A, MPArgs m) {
+template <typename R> __global__ void k_qupdate(CaseArgs A, MPArgs m) {
   const long long n = (long long)A.nx * A.ny;
   const long long nfx = (long long)(A.nx + 1) * A.ny, nfy = (long long)A.nx * (A.ny + 1);
-  const double *ax = m.qfx + QF_AX * nfx, *ay = m.qfx + QF_AY * nfx;
-  const double *bx = m.qfy + QF_AX * nfy, *by = m.qfy + QF_AY * nfy;
-  double *fo = (double *)A.fout;
+  const R *qfx = (const R *)m.qfx, *qfy = (const R *)m.qfy;
+  const R *ax = qfx + QF_AX * nfx, *ay = qfx + QF_AY * nfx;
+  const R *bx = qfy + QF_AX * nfy, *by = qfy + QF_AY * nfy;
+  const R *tp = (const R *)m.tp, *fx = (const R *)m.fx, *fy = (const R *)m.fy, *vsc = (const R *)m.vs;
+  R *fo = (R *)A.fout;
   for (long long k = blockIdx.x * (long long)T + threadIdx.x; k < n; k += (long long)gridDim.x * T) {
     const int j = (int)(k / A.nx), i = (int)(k % A.nx);
     const long long w = (long long)j * (A.nx + 1) + i, s = (long long)j * A.nx + i, nn = s + A.nx;
-    const double vs = m.vs[k];
+    const R vs = vsc[k];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const double flux = (EX(a) * ax[w + 1] + EY(a) * ay[w + 1]) * m.fx[a * nfx + w + 1] -
-                          (EX(a) * ax[w] + EY(a) * ay[w]) * m.fx[a * nfx + w] +
-                          (EX(a) * bx[nn] + EY(a) * by[nn]) * m.fy[a * nfy + nn] -
-                          (EX(a) * bx[s] + EY(a) * by[s]) * m.fy[a * nfy + s];
-      fo[a * A.plane + (long long)j * A.pitch + i] = m.tp[a * n + k] - vs * flux;
+      const R ex = R(EX(a)), ey = R(EY(a));
+      const R flux = (ex * ax[w + 1] + ey * ay[w + 1]) * fx[a * nfx + w + 1] -
+                     (ex * ax[w] + ey * ay[w]) * fx[a * nfx + w] +
+                     (ex * bx[nn] + ey * by[nn]) * fy[a * nfy + nn] -
+                     (ex * bx[s] + ey * by[s]) * fy[a * nfy + s];
+      fo[a * A.plane + (long long)j * A.pitch + i] = tp[a * n + k] - vs * flux;
     }
   }
 }
@@ -449,24 +480,28 @@ int grid(long long n) {
 
 } // namespace mp
 
-cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s) {
+template <typename R> static cudaError_t launch_mp(const CaseArgs &a, const MPArgs &m, cudaStream_t s) {
   using namespace mp;
   if (m.quad) {
-    k_stage<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
-    k_qghost_x<<<grid(a.ny), T, 0, s>>>(a, m);
-    k_qghost_y<<<grid(a.nx + 4), T, 0, s>>>(a, m);
-    k_qfaces_x<<<grid((long long)(a.nx + 1) * a.ny), T, 0, s>>>(a, m);
-    k_qfaces_y<<<grid((long long)a.nx * (a.ny + 1)), T, 0, s>>>(a, m);
-    k_qupdate<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+    k_stage<R><<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+    k_qghost_x<R><<<grid(a.ny), T, 0, s>>>(a, m);
+    k_qghost_y<R><<<grid(a.nx + 4), T, 0, s>>>(a, m);
+    k_qfaces_x<R><<<grid((long long)(a.nx + 1) * a.ny), T, 0, s>>>(a, m);
+    k_qfaces_y<R><<<grid((long long)a.nx * (a.ny + 1)), T, 0, s>>>(a, m);
+    k_qupdate<R><<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
     return cudaGetLastError();
   }
-  k_stage<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
-  k_ghost_x<<<grid(a.ny), T, 0, s>>>(a, m);
-  k_ghost_y<<<grid(a.nx + 4), T, 0, s>>>(a, m);
-  k_faces_x<<<grid((long long)(a.nx + 1) * a.ny), T, 0, s>>>(a, m);
-  k_faces_y<<<grid((long long)a.nx * (a.ny + 1)), T, 0, s>>>(a, m);
-  k_update<<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+  k_stage<R><<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
+  k_ghost_x<R><<<grid(a.ny), T, 0, s>>>(a, m);
+  k_ghost_y<R><<<grid(a.nx + 4), T, 0, s>>>(a, m);
+  k_faces_x<R><<<grid((long long)(a.nx + 1) * a.ny), T, 0, s>>>(a, m);
+  k_faces_y<R><<<grid((long long)a.nx * (a.ny + 1)), T, 0, s>>>(a, m);
+  k_update<R><<<grid((long long)a.nx * a.ny), T, 0, s>>>(a, m);
   return cudaGetLastError();
+}
+
+cudaError_t launch_multipass(const CaseArgs &a, const MPArgs &m, cudaStream_t s) {
+  return m.elem == 8 ? launch_mp<double>(a, m, s) : launch_mp<float>(a, m, s);
 }
 
 } // namespace dvbe
