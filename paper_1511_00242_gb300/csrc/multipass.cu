@@ -1,7 +1,7 @@
-// Multi-pass FP64 step with face arrays: the form of the step the paper's
-// implementation keeps ("two sets of additional DFs and macro variables at
-// cell faces", Sec 3.1), one kernel per stage, for the reconstruction
-// variants the fused strip kernel does not carry.
+// Multi-pass step with face arrays, one kernel per stage: the form of the
+// paper's own implementation, which holds extra arrays of distributions and
+// moments at the cell faces (Sec 3.1).  It carries the reconstruction
+// variants and the quadrilateral meshes the fused strip kernel does not.
 //
 //   1. cell stage: phi (f_bar^+ for DUGKS, f_tilde^+ for BKG, the cell f^n
 //      for the collision-free faces) into a padded array with two ghost
