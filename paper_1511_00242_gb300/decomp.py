@@ -136,7 +136,10 @@ class Block:
 
 
 def plan(case, PX: int, PY: int):
-    """Blocks of a PX x PY decomposition of `case`; rank = by * PX + bx."""
+    """Blocks of a PX x PY decomposition of `case` (a tensor mesh given by its
+    face coordinates); rank = by * PX + bx."""
+    if "xf" not in case or "yf" not in case:
+        raise ValueError("the decomposition splits tensor meshes (face coordinates xf, yf) only")
     xs, ys = _split(case["nx"], PX), _split(case["ny"], PY)
     return [Block(by * PX + bx, bx, by, xs[bx], ys[by], case, PX, PY)
             for by in range(PY) for bx in range(PX)]

@@ -122,6 +122,8 @@ def test_plan_covers_the_mesh_once():
         assert (cover == 1).all()
     with pytest.raises(ValueError):
         decomp.plan(case, 14, 1)  # blocks of fewer than 2 cells
+    with pytest.raises(ValueError):  # quadrilateral meshes are not split
+        decomp.plan(W.quad_from_faces(case), 2, 1)
 
 
 def _free_port():
