@@ -308,3 +308,14 @@ def test_planted_quad_mistakes_are_caught(tmp_path, name):
     assert failed, f"mutation {name} passed every pin"
     if name in QTARGETED:
         assert QTARGETED[name] in failed, (name, failed)
+
+
+@pytest.mark.parametrize("RTv", [0.2, 0.7])
+def test_quad_step_reduces_to_the_tensor_oracle_at_other_RT(RTv):
+    """The same reduction with the lattice speed c = sqrt(3 RT) away from 1:
+    walls with a moving lid, a free stream and a symmetry side."""
+    for name in ("cavity", "plate"):
+        case = dict(TENSOR[name], RT=RTv, recon="linear")
+        case["dt"] = W.cfl_dt(case["xf"], case["yf"], 0.5, RT=RTv)
+        f0 = _state(case, 8)
+        assert rel(O.quad_step(W.quad_from_faces(case), f0, 5), O.step(case, f0, 5)) < 1e-13, name
